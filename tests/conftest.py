@@ -1,0 +1,19 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+for p in (ROOT, os.path.join(ROOT, "tests")):
+    if p not in sys.path:
+        sys.path.insert(0, p)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
+
+
+def pytest_collection_modifyitems(config, items):
+    # A gpu-marked test is never silently skipped on a GPU machine; on a CPU-only
+    # machine the marker expression (-m "not gpu") deselects it.
+    pass
