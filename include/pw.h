@@ -1,0 +1,210 @@
+/*
+ * pw.h — C ABI of the GB300 library for the Piacsek-Williams (PW) advection
+ * scheme (Sec. 2.2 of "Exploring the Versal AI engines for accelerating
+ * stencil-based atmospheric advection simulation").
+ *
+ * The scheme: given the three velocity fields u, v, w on a 3D grid with one
+ * halo cell, compute the advective source terms su, sv, sw; a depth-one
+ * stencil over all three dimensions (Sec. 2.2), per cell and field six pair
+ * sums, six products, scaled differences and a final sum (Sec. 4).  The
+ * scheme's index pattern (Arakawa-C staggering, u on +x faces, v on +y
+ * faces, w on the top face of each layer):
+ *
+ *   su = tcx [u(i-1)(u+u(i-1)) - u(i+1)(u+u(i+1))]
+ *      + tcy [u(j-1)(v(j-1)+v(j-1,i+1)) - u(j+1)(v+v(i+1))]
+ *      + tzc1[k] u(k-1)(w(k-1)+w(k-1,i+1)) - tzc2[k] u(k+1)(w+w(i+1))
+ *   sv = tcx [v(i-1)(u(i-1)+u(j+1,i-1)) - v(i+1)(u+u(j+1))]
+ *      + tcy [v(j-1)(v+v(j-1)) - v(j+1)(v+v(j+1))]
+ *      + tzc1[k] v(k-1)(w(k-1)+w(k-1,j+1)) - tzc2[k] v(k+1)(w+w(j+1))
+ *   sw = tcx [w(i-1)(u(i-1)+u(k+1,i-1)) - w(i+1)(u+u(k+1))]
+ *      + tcy [w(j-1)(v(j-1)+v(k+1,j-1)) - w(j+1)(v+v(k+1))]
+ *      + tzd1[k] w(k-1)(w+w(k-1)) - tzd2[k] w(k+1)(w+w(k+1))
+ *
+ * (offsets relative to (k, j, i)); su, sv at k = 2..nz with the upper vertical
+ * term dropped at the lid k = nz; sw at k = 2..nz-1; su, sv at k = 1 and sw at
+ * k = 1, nz are written as 0.  The halo cells of su, sv, sw are never written;
+ * the z-halo planes k = 0 and nz+1 of u, v, w are never read.
+ *
+ * Conventions for every entry point:
+ *   - Return a pw_status_t; on failure pw_last_error() (thread-local) holds a
+ *     message.  Argument errors are detected on the host before any launch.
+ *   - Field pointers are DEVICE pointers to caller-owned memory (for example
+ *     torch tensors), unless an entry point says HOST.  The library never
+ *     frees them.  Outputs must not alias inputs.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t cast to void*; NULL is
+ *     the legacy default stream).  A kernel that gives up a bounded wait
+ *     records it in the handle; pw_sync() reports it as PW_ERR_DEVICE_TIMEOUT.
+ *   - A handle is bound to the device that was current at pw_create(); that
+ *     device must be current for every call with the handle.
+ */
+#ifndef PW_H
+#define PW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PW_OK = 0,
+    PW_ERR_ARG = 1,             /* invalid argument (null, size, layout) */
+    PW_ERR_ALIGN = 2,           /* pointer or pitch alignment not met */
+    PW_ERR_CUDA = 3,            /* a CUDA runtime/driver call failed */
+    PW_ERR_OOM = 4,             /* device or host allocation failed */
+    PW_ERR_DEVICE_TIMEOUT = 5,  /* a kernel gave up a bounded wait */
+    PW_ERR_UNSUPPORTED = 6      /* valid request this build does not implement */
+} pw_status_t;
+
+/* Storage type of the fields in device memory.  Arithmetic is always FP32. */
+typedef enum { PW_F32 = 0, PW_BF16 = 1, PW_F16 = 2 } pw_dtype_t;
+
+/*
+ * Grid and field layout, shared by all six fields of a call.
+ * Element (k, j, i) of a field sits at
+ *     ptr[origin + k*pitch_k + j*pitch_j + i]          (element units)
+ * with interior i = 1..nx, j = 1..ny, k = 1..nz, lateral halo i in
+ * [1-halo, 0] and [nx+1, nx+halo] (likewise j), z halo k = 0 and nz+1.
+ * Requirements: nx, ny >= 1, nz >= 3, halo >= 1, pitch_j >= nx + 2*halo,
+ * pitch_k >= pitch_j*(ny + 2*halo), origin >= (halo-1)*(pitch_j + 1).
+ * The scheme reads one halo cell; a deeper halo is room for the periodic
+ * images that multi-step updates write.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t halo;
+    int64_t pitch_j;   /* elements between rows (j) */
+    int64_t pitch_k;   /* elements between levels (k) */
+    int64_t origin;    /* element offset of (k=0, j=0, i=0) from the pointer */
+    pw_dtype_t dtype;
+} pw_grid_t;
+
+/* Scheme coefficients (Sec. 2.2), copied at pw_create (the caller keeps
+ * ownership of its arrays): tcx, tcy scalars; tzc1, tzc2, tzd1, tzd2 HOST
+ * arrays of nz+2 doubles indexed by k (k = 0..nz+1; entries the scheme does
+ * not use are ignored).  Converted to FP32 for the device arithmetic. */
+typedef struct {
+    double tcx, tcy;
+    const double *tzc1, *tzc2, *tzd1, *tzd2;
+} pw_coeffs_t;
+
+typedef struct pw_handle_s *pw_handle_t;
+typedef void *pw_stream_t; /* cudaStream_t */
+
+/*
+ * Default layout for (nx, ny, nz, halo, dtype): interior rows start on a
+ * 128-byte boundary, pitch_j a multiple of 128 bytes.  Writes the grid to
+ * *out and the number of elements each field allocation must hold to
+ * *alloc_elems (may be NULL).  This layout qualifies for the TMA k-march
+ * kernel when nx is a multiple of 4.
+ */
+pw_status_t pw_grid_default(int32_t nx, int32_t ny, int32_t nz, int32_t halo, pw_dtype_t dtype,
+                            pw_grid_t *out, int64_t *alloc_elems);
+
+/*
+ * Create a handle for one grid and coefficient set on the current device.
+ * Validates the layout, copies the coefficients to device memory, allocates
+ * the handle's status word.  *out is NULL on failure.
+ */
+pw_status_t pw_create(const pw_grid_t *grid, const pw_coeffs_t *coeffs, pw_handle_t *out);
+
+/* Release the handle and everything it allocated.  NULL is accepted. */
+pw_status_t pw_destroy(pw_handle_t h);
+
+/* Kernel selection for pw_tendencies: 0 = automatic (TMA k-march kernel when
+ * the layout and pointers qualify, else the generic kernel), 1 = generic
+ * kernel, 2 = TMA kernel (PW_ERR_UNSUPPORTED/PW_ERR_ALIGN at call time when
+ * the layout or pointers do not qualify). */
+pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
+
+/*
+ * Launch shape of the TMA k-march kernel: ty = rows per CTA (4, 8 or 16),
+ * stages = planes buffered per CTA (3..6), nseg = CTAs along z (0 = chosen
+ * from the grid and SM count).  Any argument 0 keeps the automatic choice.
+ */
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t ty, int32_t stages, int32_t nseg);
+
+/*
+ * Source terms su, sv, sw of the PW scheme (Sec. 2.2; arithmetic shape
+ * Sec. 4) from u, v, w, all in the handle's layout and dtype, halo cells of
+ * the inputs used as given (refresh them first, e.g. with
+ * pw_fill_halo_periodic).  scale: NULL, or 6 floats
+ * {in_u, in_v, in_w, out_su, out_sv, out_sw}: the physical value of a stored
+ * input is stored*in; the stored output is physical*out (powers of two keep
+ * this exact).  Interior cells of su, sv, sw are written, halos untouched.
+ */
+pw_status_t pw_tendencies(pw_handle_t h, const void *u, const void *v, const void *w,
+                          void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
+
+/*
+ * pw_tendencies on HOST buffers (pageable or pinned) in the handle's layout:
+ * copies u, v, w to device buffers the handle owns (allocated and zeroed on
+ * first use), computes, copies su, sv, sw back, and returns when the results
+ * are in host memory.  Per field, the contiguous span of levels 1..nz, from
+ * element (1, 1-halo, 1-halo) to element (nz, ny+halo, nx+halo), travels
+ * each way (the z-halo planes are never read); cells of that span outside
+ * the interior come back as 0 in su, sv, sw.
+ */
+pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, const void *w,
+                               void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
+
+/*
+ * Periodic lateral boundary: copy interior values into the lateral halo of
+ * f (all halo columns and rows, corners included, levels k = 1..nz), as the
+ * halo swap of a doubly periodic domain before each evaluation of the scheme
+ * (Sec. 2.2 describes the scheme as called every model timestep).
+ */
+pw_status_t pw_fill_halo_periodic(pw_handle_t h, void *f, pw_stream_t stream);
+
+/*
+ * Validation norms in FP64 over the interior cells of levels k0..k1
+ * (1 <= k0 <= k1 <= nz): for a field `test` in the handle's dtype (scaled by
+ * `scale`: physical = stored*scale) and a DEVICE FP64 reference `ref` in the
+ * dense layout (nz+2, ny+2, nx+2) (element (k,j,i) at
+ * ((k*(ny+2)+j)*(nx+2)+i)), writes out[0] = max |test - ref|,
+ * out[1] = max |ref|, out[2] = sum (test - ref)^2, out[3] = sum ref^2
+ * (out: HOST array of 4 doubles).  Synchronises `stream`.
+ * Uses a scratch buffer the handle allocates on first use.
+ */
+pw_status_t pw_error_norms(pw_handle_t h, const void *test, float scale, const double *ref,
+                           int32_t k0, int32_t k1, double *out, pw_stream_t stream);
+
+/*
+ * Weighted inner product in FP64 over interior cells of levels k0..k1:
+ * returns in *out  sum_k wk[k] * sum_{j,i} a(k,j,i) * b(k,j,i)  for two fields
+ * in the handle's layout and dtype (scales sa, sb as in pw_error_norms);
+ * wk is a HOST array of nz+2 doubles (NULL = all ones).  Used for the
+ * discrete energy identity of the scheme.  Synchronises `stream`.
+ */
+pw_status_t pw_weighted_dot(pw_handle_t h, const void *a, float sa, const void *b, float sb,
+                            const double *wk, int32_t k0, int32_t k1, double *out, pw_stream_t stream);
+
+/* Wait for `stream`, then report (and clear) any bounded-wait timeout a
+ * kernel of this handle recorded, and any pending CUDA error. */
+pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream);
+
+/*
+ * Self-test of failure detection (no counterpart in the paper): launches a
+ * one-warp kernel that waits on a barrier phase nothing completes, gives up
+ * after limit_ns nanoseconds (1e6..1e9) and records a timeout in the handle,
+ * as a kernel whose copy never lands would.  The next pw_sync() returns
+ * PW_ERR_DEVICE_TIMEOUT and clears it; the CUDA context stays usable.
+ */
+pw_status_t pw_selftest_wait_timeout(pw_handle_t h, int64_t limit_ns, pw_stream_t stream);
+
+/* Message for the last failure on this thread ("" if none). */
+const char *pw_last_error(void);
+
+/* Static name of a status code. */
+const char *pw_status_string(pw_status_t s);
+
+/* Which kernel the last pw_tendencies call on this handle launched:
+ * 1 = generic, 2 = TMA k-march, 0 = none yet. */
+int32_t pw_last_kernel(pw_handle_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PW_H */

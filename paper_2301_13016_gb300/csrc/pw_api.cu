@@ -1,0 +1,476 @@
+// C ABI of the PW library: handles, argument validation, TMA descriptors,
+// kernel selection and launch.  See include/pw.h for the contract.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pw_device.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+size_t dtype_size(pw_dtype_t t) { return t == PW_F32 ? 4 : 2; }
+
+static thread_local std::string g_err;
+
+static pw_status_t fail(pw_status_t s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+static pw_status_t cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? PW_ERR_OOM : PW_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define PW_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+struct MapCacheEntry {
+    const void* ptr = nullptr;
+    int ty = 0;
+    CUtensorMap map;
+};
+
+}  // namespace pw
+
+using namespace pw;
+
+struct pw_handle_s {
+    pw_grid_t grid;
+    int device = 0;
+    int num_sms = 0;
+    float tcx = 0.f, tcy = 0.f;
+    float* d_tz = nullptr;      // tzc1 | tzc2 | tzd1 | tzd2, nz+2 each
+    int* d_err = nullptr;       // device status word (bounded-wait timeouts)
+    int kernel_kind = 0;        // 0 auto, 1 generic, 2 TMA
+    int last_kernel = 0;
+    TmaConfig tma_user{0, 0, 0};
+    TmaConfig tma_auto{0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
+    MapCacheEntry maps[3];
+    // pw_tendencies_host staging
+    void* d_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // validation scratch: 4*(nblocks+1) doubles + wk (nz+2 doubles)
+    double* d_scratch = nullptr;
+    int nblocks = 0;
+};
+
+static GridDev to_dev(const pw_grid_t& g) {
+    GridDev d;
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.nz = g.nz;
+    d.halo = g.halo;
+    d.pj = g.pitch_j;
+    d.pk = g.pitch_k;
+    d.origin = g.origin;
+    return d;
+}
+
+// Element count a field allocation must hold for this layout.
+static long long alloc_elems_of(const pw_grid_t& g) {
+    return g.origin + (long long)(g.nz + 1) * g.pitch_k + (long long)(g.ny + g.halo) * g.pitch_j + g.nx + g.halo +
+           1;
+}
+
+static pw_status_t validate_grid(const pw_grid_t* g) {
+    if (!g) return fail(PW_ERR_ARG, "grid is NULL");
+    if (g->dtype != PW_F32 && g->dtype != PW_BF16 && g->dtype != PW_F16)
+        return fail(PW_ERR_ARG, "unknown dtype %d", (int)g->dtype);
+    if (g->nx < 1 || g->ny < 1) return fail(PW_ERR_ARG, "nx, ny must be >= 1 (got %d, %d)", g->nx, g->ny);
+    if (g->nz < 3) return fail(PW_ERR_ARG, "nz must be >= 3 (got %d)", g->nz);
+    if (g->halo < 1) return fail(PW_ERR_ARG, "halo must be >= 1 (got %d)", g->halo);
+    if (g->halo > g->nx || g->halo > g->ny)
+        return fail(PW_ERR_ARG, "halo %d exceeds the interior (%d x %d)", g->halo, g->nx, g->ny);
+    if (g->pitch_j < (long long)g->nx + 2 * g->halo)
+        return fail(PW_ERR_ARG, "pitch_j %lld < nx + 2*halo", (long long)g->pitch_j);
+    if (g->pitch_k < g->pitch_j * ((long long)g->ny + 2 * g->halo))
+        return fail(PW_ERR_ARG, "pitch_k %lld < pitch_j*(ny + 2*halo)", (long long)g->pitch_k);
+    if (g->origin < (long long)(g->halo - 1) * (g->pitch_j + 1))
+        return fail(PW_ERR_ARG, "origin %lld leaves no room for the halo", (long long)g->origin);
+    return PW_OK;
+}
+
+// TMA eligibility of the layout (pointer alignment is checked per call).
+// Writes the x offset `ox` of element i = 0 within its padded row.
+static bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
+    const long long es = (long long)dtype_size(g.dtype);
+    const long long padx = 16 / es;
+    if (g.nx % 4) { *why = "nx is not a multiple of 4"; return false; }
+    if ((g.pitch_j * es) % 16 || (g.pitch_k * es) % 16) { *why = "pitches are not multiples of 16 bytes"; return false; }
+    const long long r = g.origin - (long long)(g.halo - 1) * g.pitch_j;
+    if (r < 0 || r >= g.pitch_j) { *why = "origin is not within the first padded row"; return false; }
+    if ((r + 1) % padx) { *why = "interior rows do not start on a 16-byte boundary"; return false; }
+    if (r + g.nx + g.halo + 1 > g.pitch_j) { *why = "row does not fit its pitch"; return false; }
+    if (g.nz + 2 > (1 << 30) || g.ny + 2 * g.halo > (1 << 30)) { *why = "grid too large for a tensor map"; return false; }
+    *ox_out = (int)r;
+    return true;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static pw_status_t encode_map(pw_handle_t h, int slot, const void* ptr, int ox, int ty, CUtensorMap* out) {
+    MapCacheEntry& e = h->maps[slot];
+    if (e.ptr == ptr && e.ty == ty) {
+        *out = e.map;
+        return PW_OK;
+    }
+    auto fn = encode_fn();
+    if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const pw_grid_t& g = h->grid;
+    const size_t es = dtype_size(g.dtype);
+    CUtensorMapDataType dt = g.dtype == PW_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : g.dtype == PW_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)(ox + g.nx + g.halo + 1), (cuuint64_t)(g.ny + 2 * g.halo),
+                          (cuuint64_t)(g.nz + 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)(g.pitch_j * es), (cuuint64_t)(g.pitch_k * es)};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(out, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    e.ptr = ptr;
+    e.ty = ty;
+    e.map = *out;
+    return PW_OK;
+}
+
+// Launch shape of the TMA kernel: user overrides, else ty = 8, 4 stages, and
+// enough k segments for about two waves of CTAs over the SMs.
+static TmaConfig choose_tma(pw_handle_t h) {
+    if (h->tma_auto.ty) return h->tma_auto;
+    TmaConfig c;
+    c.ty = h->tma_user.ty ? h->tma_user.ty : 8;
+    c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
+    if (h->tma_user.nseg) {
+        c.nseg = h->tma_user.nseg;
+    } else {
+        const long long tiles = (long long)((h->grid.nx + 127) / 128) * ((h->grid.ny + c.ty - 1) / c.ty);
+        int bps = tma_blocks_per_sm(h->grid.dtype, c);
+        if (bps < 1) bps = 1;
+        const long long slots = (long long)h->num_sms * bps;
+        int nseg = 1;
+        while (tiles * nseg < 2 * slots && h->grid.nz / (nseg * 2) >= 8) nseg *= 2;
+        c.nseg = nseg;
+    }
+    if (c.nseg > h->grid.nz / 2) c.nseg = std::max(1, h->grid.nz / 2);
+    h->tma_auto = c;
+    return c;
+}
+
+static void make_scales(const float* scale, Scales* sc, bool* scaled) {
+    *scaled = false;
+    for (int q = 0; q < 3; ++q) {
+        sc->in[q] = scale ? scale[q] : 1.f;
+        sc->out[q] = scale ? scale[3 + q] : 1.f;
+        if (sc->in[q] != 1.f || sc->out[q] != 1.f) *scaled = true;
+    }
+}
+
+extern "C" {
+
+pw_status_t pw_grid_default(int32_t nx, int32_t ny, int32_t nz, int32_t halo, pw_dtype_t dtype, pw_grid_t* out,
+                            int64_t* alloc_elems) {
+    if (!out) return fail(PW_ERR_ARG, "out is NULL");
+    if (dtype != PW_F32 && dtype != PW_BF16 && dtype != PW_F16) return fail(PW_ERR_ARG, "unknown dtype");
+    if (nx < 1 || ny < 1 || nz < 3 || halo < 1) return fail(PW_ERR_ARG, "need nx, ny >= 1, nz >= 3, halo >= 1");
+    const long long line = 128 / (long long)dtype_size(dtype);   // elements per 128 bytes
+    // interior i = 1 at x = ox + 1, a multiple of `line`, with room for the halo
+    const long long ox = ((halo + line - 1) / line) * line - 1;
+    const long long pj = ((ox + 1 + nx + halo + line - 1) / line) * line;
+    const long long pk = pj * (ny + 2LL * halo);
+    pw_grid_t g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.halo = halo;
+    g.pitch_j = pj;
+    g.pitch_k = pk;
+    g.origin = ox + (long long)(halo - 1) * pj;
+    g.dtype = dtype;
+    *out = g;
+    if (alloc_elems) *alloc_elems = pk * (nz + 2LL);
+    return PW_OK;
+}
+
+pw_status_t pw_create(const pw_grid_t* grid, const pw_coeffs_t* coeffs, pw_handle_t* out) {
+    if (!out) return fail(PW_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    pw_status_t s = validate_grid(grid);
+    if (s != PW_OK) return s;
+    if (!coeffs || !coeffs->tzc1 || !coeffs->tzc2 || !coeffs->tzd1 || !coeffs->tzd2)
+        return fail(PW_ERR_ARG, "coefficients or one of the vertical coefficient arrays is NULL");
+    pw_handle_s* h = new (std::nothrow) pw_handle_s();
+    if (!h) return fail(PW_ERR_OOM, "host allocation of the handle failed");
+    h->grid = *grid;
+    h->tcx = (float)coeffs->tcx;
+    h->tcy = (float)coeffs->tcy;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int n = grid->nz + 2;
+    std::vector<float> tz(4 * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        tz[k] = (float)coeffs->tzc1[k];
+        tz[n + k] = (float)coeffs->tzc2[k];
+        tz[2 * n + k] = (float)coeffs->tzd1[k];
+        tz[3 * n + k] = (float)coeffs->tzd2[k];
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_tz, tz.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        pw_destroy(h);
+        return cuda_fail(e, "pw_create");
+    }
+    *out = h;
+    return PW_OK;
+}
+
+pw_status_t pw_destroy(pw_handle_t h) {
+    if (!h) return PW_OK;
+    cudaFree(h->d_tz);
+    cudaFree(h->d_err);
+    for (auto& p : h->d_stage) cudaFree(p);
+    cudaFree(h->d_scratch);
+    delete h;
+    return PW_OK;
+}
+
+pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (kind < 0 || kind > 2) return fail(PW_ERR_ARG, "kernel kind must be 0, 1 or 2");
+    h->kernel_kind = kind;
+    return PW_OK;
+}
+
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t ty, int32_t stages, int32_t nseg) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
+    TmaConfig c{ty ? ty : 8, stages ? stages : 4, 1};
+    if (!tma_config_supported(h->grid.dtype, c))
+        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for ty=%d stages=%d", c.ty, c.stages);
+    h->tma_user = TmaConfig{ty, stages, nseg};
+    h->tma_auto = TmaConfig{0, 0, 0};
+    for (auto& m : h->maps) m.ptr = nullptr;
+    return PW_OK;
+}
+
+int32_t pw_last_kernel(pw_handle_t h) { return h ? h->last_kernel : 0; }
+
+pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
+                          void* sw, const float* scale, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (!u || !v || !w || !su || !sv || !sw) return fail(PW_ERR_ARG, "a field pointer is NULL");
+    const void* ins[3] = {u, v, w};
+    const void* outs[3] = {su, sv, sw};
+    for (auto o : outs)
+        for (auto i : ins)
+            if (o == i) return fail(PW_ERR_ARG, "an output aliases an input");
+    if (su == sv || su == sw || sv == sw) return fail(PW_ERR_ARG, "outputs alias each other");
+    if (scale)
+        for (int q = 0; q < 6; ++q)
+            if (!(scale[q] > 0.f) || !(scale[q] < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
+    Scales sc;
+    bool scaled;
+    make_scales(scale, &sc, &scaled);
+    const GridDev g = to_dev(h->grid);
+    CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    int ox = 0;
+    const char* why = "";
+    bool layout_ok = tma_layout_ok(h->grid, &ox, &why);
+    bool ptrs_ok = true;
+    for (auto p : ins) ptrs_ok = ptrs_ok && aligned16(p);
+    for (auto p : outs) ptrs_ok = ptrs_ok && aligned16(p);
+    bool use_tma = (h->kernel_kind == 2) || (h->kernel_kind == 0 && layout_ok && ptrs_ok);
+    if (h->kernel_kind == 2) {
+        if (!layout_ok) return fail(PW_ERR_UNSUPPORTED, "TMA kernel requested but %s", why);
+        if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
+    }
+    if (use_tma) {
+        TmaConfig c = choose_tma(h);
+        CUtensorMap maps[3];
+        for (int q = 0; q < 3; ++q) {
+            pw_status_t st = encode_map(h, q, ins[q], ox, c.ty, &maps[q]);
+            if (st != PW_OK) return st;
+        }
+        cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, scaled, cf, h->d_err, c, s);
+        if (e != cudaSuccess) return cuda_fail(e, "TMA tendency kernel launch");
+        h->last_kernel = 2;
+    } else {
+        cudaError_t e = launch_tend_generic(h->grid.dtype, g, u, v, w, su, sv, sw, sc, scaled, cf, h->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "generic tendency kernel launch");
+        h->last_kernel = 1;
+    }
+    return PW_OK;
+}
+
+pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
+                               void* sw, const float* scale, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (!u || !v || !w || !su || !sv || !sw) return fail(PW_ERR_ARG, "a field pointer is NULL");
+    const pw_grid_t& g = h->grid;
+    const size_t es = dtype_size(g.dtype);
+    const size_t bytes = (size_t)alloc_elems_of(g) * es;
+    for (auto& p : h->d_stage)
+        if (!p) {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging allocation");
+            e = cudaMemset(p, 0, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging clear");
+        }
+    // levels 1..nz (the z-halo planes are never read), full padded rows
+    const size_t lo = (size_t)(g.origin + g.pitch_k + (long long)(1 - g.halo) * g.pitch_j + 1 - g.halo);
+    const size_t hi = (size_t)(g.origin + (long long)g.nz * g.pitch_k + (long long)(g.ny + g.halo) * g.pitch_j +
+                               g.nx + g.halo + 1);
+    const size_t off = lo * es, len = (hi - lo) * es;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const void* hin[3] = {u, v, w};
+    void* hout[3] = {su, sv, sw};
+    for (int q = 0; q < 3; ++q)
+        PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len, cudaMemcpyHostToDevice, s),
+                "pw_tendencies_host input copy");
+    pw_status_t st = pw_tendencies(h, h->d_stage[0], h->d_stage[1], h->d_stage[2], h->d_stage[3], h->d_stage[4],
+                                   h->d_stage[5], scale, stream);
+    if (st != PW_OK) return st;
+    for (int q = 0; q < 3; ++q)
+        PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len, cudaMemcpyDeviceToHost, s),
+                "pw_tendencies_host output copy");
+    PW_CUDA(cudaStreamSynchronize(s), "pw_tendencies_host synchronize");
+    return PW_OK;
+}
+
+pw_status_t pw_fill_halo_periodic(pw_handle_t h, void* f, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (!f) return fail(PW_ERR_ARG, "field pointer is NULL");
+    cudaError_t e = launch_fill_halo(h->grid.dtype, to_dev(h->grid), f, h->num_sms,
+                                     reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
+    return PW_OK;
+}
+
+static pw_status_t ensure_scratch(pw_handle_t h) {
+    if (h->d_scratch) return PW_OK;
+    h->nblocks = norm_blocks(h->num_sms);
+    const size_t n = 4 * (size_t)(h->nblocks + 1) + (size_t)(h->grid.nz + 2);
+    cudaError_t e = cudaMalloc(&h->d_scratch, n * sizeof(double));
+    if (e != cudaSuccess) {
+        h->d_scratch = nullptr;
+        return cuda_fail(e, "validation scratch allocation");
+    }
+    return PW_OK;
+}
+
+pw_status_t pw_error_norms(pw_handle_t h, const void* test, float scale, const double* ref, int32_t k0, int32_t k1,
+                           double* out, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (!test || !ref || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
+    if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
+    pw_status_t st = ensure_scratch(h);
+    if (st != PW_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_error_norms(h->grid.dtype, to_dev(h->grid), test, scale, ref, k0, k1, h->d_scratch,
+                                       h->nblocks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "norm kernel launch");
+    PW_CUDA(cudaMemcpyAsync(out, h->d_scratch + 4 * (size_t)h->nblocks, 4 * sizeof(double), cudaMemcpyDeviceToHost, s),
+            "norm result copy");
+    PW_CUDA(cudaStreamSynchronize(s), "norm synchronize");
+    return PW_OK;
+}
+
+pw_status_t pw_weighted_dot(pw_handle_t h, const void* a, float sa, const void* b, float sb, const double* wk,
+                            int32_t k0, int32_t k1, double* out, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (!a || !b || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
+    if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
+    pw_status_t st = ensure_scratch(h);
+    if (st != PW_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double* d_wk = nullptr;
+    if (wk) {
+        d_wk = h->d_scratch + 4 * (size_t)(h->nblocks + 1);
+        PW_CUDA(cudaMemcpyAsync(d_wk, wk, (h->grid.nz + 2) * sizeof(double), cudaMemcpyHostToDevice, s),
+                "weight copy");
+    }
+    cudaError_t e = launch_weighted_dot(h->grid.dtype, to_dev(h->grid), a, sa, b, sb, d_wk, k0, k1, h->d_scratch,
+                                        h->nblocks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dot kernel launch");
+    double r[4];
+    PW_CUDA(cudaMemcpyAsync(r, h->d_scratch + 4 * (size_t)h->nblocks, 4 * sizeof(double), cudaMemcpyDeviceToHost, s),
+            "dot result copy");
+    PW_CUDA(cudaStreamSynchronize(s), "dot synchronize");
+    out[0] = r[2];
+    return PW_OK;
+}
+
+pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    PW_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "stream synchronize");
+    int flag = 0;
+    PW_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status word read");
+    if (flag != DEV_OK) {
+        PW_CUDA(cudaMemset(h->d_err, 0, sizeof(int)), "status word clear");
+        return fail(PW_ERR_DEVICE_TIMEOUT, "a kernel gave up a bounded wait (code %d)", flag);
+    }
+    PW_CUDA(cudaGetLastError(), "pending CUDA error");
+    return PW_OK;
+}
+
+pw_status_t pw_selftest_wait_timeout(pw_handle_t h, int64_t limit_ns, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (limit_ns < 1000000 || limit_ns > 1000000000) return fail(PW_ERR_ARG, "limit_ns must be in [1e6, 1e9]");
+    cudaError_t e = launch_selftest_wait((uint64_t)limit_ns, h->d_err, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+    return PW_OK;
+}
+
+const char* pw_last_error(void) { return g_err.c_str(); }
+
+const char* pw_status_string(pw_status_t s) {
+    switch (s) {
+        case PW_OK: return "PW_OK";
+        case PW_ERR_ARG: return "PW_ERR_ARG";
+        case PW_ERR_ALIGN: return "PW_ERR_ALIGN";
+        case PW_ERR_CUDA: return "PW_ERR_CUDA";
+        case PW_ERR_OOM: return "PW_ERR_OOM";
+        case PW_ERR_DEVICE_TIMEOUT: return "PW_ERR_DEVICE_TIMEOUT";
+        case PW_ERR_UNSUPPORTED: return "PW_ERR_UNSUPPORTED";
+    }
+    return "PW_ERR_UNKNOWN";
+}
+
+}  // extern "C"

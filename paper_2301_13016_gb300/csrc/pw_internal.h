@@ -1,0 +1,73 @@
+// Internal (non-ABI) declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pw.h"
+
+namespace pw {
+
+// Field geometry as the kernels see it: element (k, j, i) of a field sits at
+// ptr[origin + k*pk + j*pj + i], with i in [1-halo, nx+halo], j likewise,
+// k in [0, nz+1].
+struct GridDev {
+    int nx, ny, nz, halo;
+    long long pj, pk, origin;
+};
+
+// Per-field storage scales: physical = stored * in[f]; stored = physical * out[f].
+struct Scales {
+    float in[3];
+    float out[3];
+};
+
+// Scheme coefficients on the device: tz holds tzc1, tzc2, tzd1, tzd2, each
+// nz+2 floats, back to back.
+struct CoefDev {
+    float tcx, tcy;
+    const float* tz;
+};
+
+// Launch shape of the TMA k-march kernel.
+struct TmaConfig {
+    int ty;      // interior rows per CTA (one warp per row, 128 columns)
+    int stages;  // planes resident or in flight per CTA
+    int nseg;    // k segments (CTAs along z)
+};
+
+size_t dtype_size(pw_dtype_t t);
+
+cudaError_t launch_tend_generic(pw_dtype_t dt, const GridDev& g, const void* u, const void* v, const void* w,
+                                void* su, void* sv, void* sw, const Scales& sc, bool scaled,
+                                const CoefDev& cf, int num_sms, cudaStream_t s);
+
+// Box width (elements along x) of one TMA load for this dtype and the row
+// count of a box for a given ty.
+int tma_box_width(pw_dtype_t dt);
+// True if an instantiation exists for (dtype, ty, stages).
+bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c);
+size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c);
+
+cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps /*u,v,w*/,
+                            void* su, void* sv, void* sw, const Scales& sc, bool scaled, const CoefDev& cf,
+                            int* err, const TmaConfig& c, cudaStream_t s);
+
+// Blocks of the TMA kernel resident per SM for a config (0 if it cannot launch).
+int tma_blocks_per_sm(pw_dtype_t dt, const TmaConfig& c);
+
+cudaError_t launch_fill_halo(pw_dtype_t dt, const GridDev& g, void* f, int num_sms, cudaStream_t s);
+
+// Bounded-wait self-test (see pw_selftest_wait_timeout).
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int* err, cudaStream_t s);
+
+// FP64 validation reductions.  scratch holds 4*(nblocks+1) doubles; the
+// result lands in scratch[4*nblocks .. 4*nblocks+3].
+int norm_blocks(int num_sms);
+cudaError_t launch_error_norms(pw_dtype_t dt, const GridDev& g, const void* t, float scale, const double* ref,
+                               int k0, int k1, double* scratch, int nblocks, cudaStream_t s);
+cudaError_t launch_weighted_dot(pw_dtype_t dt, const GridDev& g, const void* a, float sa, const void* b, float sb,
+                                const double* wk, int k0, int k1, double* scratch, int nblocks, cudaStream_t s);
+
+}  // namespace pw
