@@ -21,6 +21,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                         J(q)d = s(q+d) - s(q) - s(d) of the pinned tendencies.
   fold_halo_periodic    pinned: dot-product test against fill_halo_periodic.
   step_adjoint          pinned: central finite differences of a rollout loss.
+  abs_terms             pinned: triangle inequality (>= |tendency|), equality
+                        for single-term inputs, quadratic scaling, and the
+                        observed rounding error of the FP32 oracle stays
+                        inside the bound it gives.
 """
 import ctypes
 import os
@@ -63,6 +67,9 @@ def _lib():
                                                    ctypes.c_double, _dp, _dp, _dp, _dp,
                                                    ctypes.c_double, i, _dp, _dp, _dp]
         lib.pw_oracle_step_adjoint_f64.restype = ctypes.c_int
+        lib.pw_oracle_abs_terms_f64.argtypes = [i, i, i, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.pw_oracle_abs_terms_f64.restype = None
         _LIB = lib
     return _LIB
 
@@ -176,9 +183,22 @@ def step_adjoint(u0, v0, w0, coeffs, dt, nsteps, gu, gv, gw):
     return gu, gv, gw
 
 
+def abs_terms(u, v, w, coeffs):
+    """Per-cell sum over the scheme's terms c*a*(b+d) of |c|*|a|*(|b|+|d|)
+    (float64; zero where the scheme writes zero): the magnitude that running
+    error bounds of the scheme scale with."""
+    u, v, w = (_arr(a, np.float64) for a in (u, v, w))
+    nx, ny, nz = _shape(u)
+    tcx, tcy, tz = _coeffs(coeffs, np.float64, nz)
+    au, av, aw = (np.zeros_like(u) for _ in range(3))
+    _lib().pw_oracle_abs_terms_f64(nx, ny, nz, _ptr(u, _dp), _ptr(v, _dp), _ptr(w, _dp), tcx, tcy,
+                                   *[_ptr(t, _dp) for t in tz], _ptr(au, _dp), _ptr(av, _dp), _ptr(aw, _dp))
+    return au, av, aw
+
+
 def library_path():
     return _build.LIB
 
 
 __all__ = ["tendencies", "fill_halo_periodic", "step", "adjoint_tendencies",
-           "fold_halo_periodic", "step_adjoint", "library_path"]
+           "fold_halo_periodic", "step_adjoint", "abs_terms", "library_path"]

@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(d) <= lib_m for d in DEPS):
             return LIB
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", LIB + ".tmp"] + SRC
+           "-fPIC", "-shared", "-o", LIB + ".tmp"] + SRC + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

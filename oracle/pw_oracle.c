@@ -18,7 +18,10 @@
  *   pw_oracle_adjoint_tendencies_f64   transpose of the linearised scheme
  *   pw_oracle_fold_halo_periodic_f64   transpose of the periodic halo swap
  *   pw_oracle_step_adjoint_f64         reverse sweep of the Euler rollout
+ *   pw_oracle_abs_terms_f64            per-cell magnitude sum of the terms
+ *                                      (running-error bounds)
  */
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -202,6 +205,53 @@ void pw_oracle_adjoint_tendencies_f64(int nx, int ny, int nz,
             }
         }
     }
+}
+
+/*
+ * Magnitude sum of the scheme's terms, for error bounds: for every output
+ * cell, the sum over its terms  c * a * (b + d)  of  |c| * |a| * (|b| + |d|)
+ * (zero where the scheme writes zero).  A perturbation of every input by a
+ * relative amount <= e changes each output by at most about 2 e times this
+ * sum (first order), and rounding the arithmetic perturbs it by a small
+ * multiple of the unit roundoff times this sum: the running-error bound the
+ * reduced-precision checks use.  Same term list and levels as the scheme.
+ */
+#define ABS3(c, a, b, d) (fabs(c) * fabs(a) * (fabs(b) + fabs(d)))
+
+void pw_oracle_abs_terms_f64(int nx, int ny, int nz,
+                             const double *u, const double *v, const double *w,
+                             double tcx, double tcy,
+                             const double *tzc1, const double *tzc2,
+                             const double *tzd1, const double *tzd2,
+                             double *au, double *av, double *aw)
+{
+    for (int k = 1; k <= nz; ++k)
+        for (int j = 1; j <= ny; ++j)
+            for (int i = 1; i <= nx; ++i) {
+                size_t c = IDX(k, j, i);
+                au[c] = 0; av[c] = 0; aw[c] = 0;
+                if (k == 1) continue;
+                au[c] = ABS3(tcx, u[IDX(k, j, i - 1)], u[IDX(k, j, i)], u[IDX(k, j, i - 1)])
+                      + ABS3(tcx, u[IDX(k, j, i + 1)], u[IDX(k, j, i)], u[IDX(k, j, i + 1)])
+                      + ABS3(tcy, u[IDX(k, j - 1, i)], v[IDX(k, j - 1, i)], v[IDX(k, j - 1, i + 1)])
+                      + ABS3(tcy, u[IDX(k, j + 1, i)], v[IDX(k, j, i)], v[IDX(k, j, i + 1)])
+                      + ABS3(tzc1[k], u[IDX(k - 1, j, i)], w[IDX(k - 1, j, i)], w[IDX(k - 1, j, i + 1)]);
+                av[c] = ABS3(tcx, v[IDX(k, j, i - 1)], u[IDX(k, j, i - 1)], u[IDX(k, j + 1, i - 1)])
+                      + ABS3(tcx, v[IDX(k, j, i + 1)], u[IDX(k, j, i)], u[IDX(k, j + 1, i)])
+                      + ABS3(tcy, v[IDX(k, j - 1, i)], v[IDX(k, j, i)], v[IDX(k, j - 1, i)])
+                      + ABS3(tcy, v[IDX(k, j + 1, i)], v[IDX(k, j, i)], v[IDX(k, j + 1, i)])
+                      + ABS3(tzc1[k], v[IDX(k - 1, j, i)], w[IDX(k - 1, j, i)], w[IDX(k - 1, j + 1, i)]);
+                if (k < nz) {
+                    au[c] += ABS3(tzc2[k], u[IDX(k + 1, j, i)], w[IDX(k, j, i)], w[IDX(k, j, i + 1)]);
+                    av[c] += ABS3(tzc2[k], v[IDX(k + 1, j, i)], w[IDX(k, j, i)], w[IDX(k, j + 1, i)]);
+                    aw[c] = ABS3(tcx, w[IDX(k, j, i - 1)], u[IDX(k, j, i - 1)], u[IDX(k + 1, j, i - 1)])
+                          + ABS3(tcx, w[IDX(k, j, i + 1)], u[IDX(k, j, i)], u[IDX(k + 1, j, i)])
+                          + ABS3(tcy, w[IDX(k, j - 1, i)], v[IDX(k, j - 1, i)], v[IDX(k + 1, j - 1, i)])
+                          + ABS3(tcy, w[IDX(k, j + 1, i)], v[IDX(k, j, i)], v[IDX(k + 1, j, i)])
+                          + ABS3(tzd1[k], w[IDX(k - 1, j, i)], w[IDX(k, j, i)], w[IDX(k - 1, j, i)])
+                          + ABS3(tzd2[k], w[IDX(k + 1, j, i)], w[IDX(k, j, i)], w[IDX(k + 1, j, i)]);
+                }
+            }
 }
 
 /*

@@ -143,7 +143,7 @@ class Grid:
         """(nz+2, ny+2*halo, nx+2*halo) view of a flat allocation; index
         [k, j+halo-1, i+halo-1] is element (k, j, i)."""
         h = self.halo
-        off = self.origin + (1 - h) * self.pitch_j + (1 - h)
+        off = flat.storage_offset() + self.origin + (1 - h) * self.pitch_j + (1 - h)
         return torch.as_strided(flat, (self.nz + 2, self.ny + 2 * h, self.nx + 2 * h),
                                 (self.pitch_k, self.pitch_j, 1), off)
 

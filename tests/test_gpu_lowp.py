@@ -1,0 +1,87 @@
+"""BF16 / FP16 storage of u, v, w and su, sv, sw with FP32 arithmetic, through
+the C ABI, against the FP64 oracle.
+
+Two per-cell bounds, with A(q) the oracle's magnitude sum of the terms
+(oracle.abs_terms) and u_s the storage format's unit roundoff:
+  kernel:  |gpu - s64(q~)| <= u_s |s64(q~)| + 2^-19 A(q~) + floor
+           (q~ = the dequantised stored inputs: only output rounding and FP32
+           arithmetic separate the two);
+  total:   |gpu - s64(q)|  <= u_s |s64(q)| + (2 u_s + 2^-19) A(q) + floor
+           (q = the original FP32 fields: adds the effect of rounding every
+           input once; the factor 1.05 on A covers the second-order terms).
+floor covers outputs that land in the format's subnormal range.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2301_13016_gb300 as pwlib
+from paper_2301_13016_gb300 import inputs, precision
+from gpu_util import NAN, interior
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_lowp(nx, ny, nz, dtype, smooth, kernel=0):
+    c = inputs.make_coeffs(nz)
+    f = inputs.smooth_fields(nx, ny, nz) if smooth else inputs.random_fields(nx, ny, nz)
+    maxabs = [float(x.abs().max()) for x in f]
+    sc = precision.suggest_scales(maxabs, c, dtype)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    h = pwlib.PW(g, c)
+    h.set_kernel(kernel)
+    dev = [g.from_dense(x, scale=s) for x, s in zip(f, sc[:3])]
+    outs = [g.alloc(fill=NAN) for _ in range(3)]
+    h.tendencies(*dev, *outs, scale=sc)
+    h.sync()
+    got = [g.to_dense(o).numpy() / s for o, s in zip(outs, sc[3:])]
+    q_tilde = [g.to_dense(d, s).numpy() for d, s in zip(dev, sc[:3])]
+    q = [x.numpy().astype(np.float64) for x in f]
+    return c, sc, q, q_tilde, got, h
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("smooth", [False, True], ids=["random", "smooth"])
+@pytest.mark.parametrize("shape", [(128, 24, 16), (388, 13, 6)], ids=["128x24x16", "388x13x6"])
+def test_lowp_storage_bounds(dtype, smooth, shape):
+    c, sc, q, qt, got, h = _run_lowp(*shape, dtype, smooth)
+    assert h.last_kernel == 2
+    us = precision.UNIT_ROUNDOFF[dtype]
+    # kernel bound: oracle on the dequantised stored inputs
+    ref_t = oracle.tendencies(*qt, c)
+    a_t = oracle.abs_terms(*qt, c)
+    for x, r, a, so in zip(got, ref_t, a_t, sc[3:]):
+        floor = 2 * precision.MIN_NORMAL[dtype] / so
+        err = np.abs(interior(x) - interior(r))
+        assert np.all(err <= us * np.abs(interior(r)) + 2.0 ** -19 * interior(a) + floor)
+    # total bound: oracle on the original FP32 fields
+    ref = oracle.tendencies(*q, c)
+    a_q = oracle.abs_terms(*q, c)
+    for x, r, a, so in zip(got, ref, a_q, sc[3:]):
+        floor = 2 * precision.MIN_NORMAL[dtype] / so
+        err = np.abs(interior(x) - interior(r))
+        assert np.all(err <= us * np.abs(interior(r)) + (2 * us + 2.0 ** -19) * interior(a) * 1.05 + floor)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_generic_matches_tma(dtype):
+    c, sc, q, qt, a, _ = _run_lowp(128, 16, 10, dtype, False, kernel=1)
+    c, sc, q, qt, b, _ = _run_lowp(128, 16, 10, dtype, False, kernel=2)
+    us = precision.UNIT_ROUNDOFF[dtype]
+    for x, y in zip(a, b):
+        # both round an FP32 result to the storage format: at most one unit apart
+        assert np.all(np.abs(interior(x) - interior(y)) <= 2 * us * np.abs(interior(y)) + 1e-30)
+
+
+def test_normwise_errors_within_stated_bounds():
+    """The normwise errors max|err|/max|ref| against the FP64 oracle on the
+    FP32 fields stay inside the stated bounds: BF16 1e-2 (random) / 1e-1
+    (smooth), FP16 2e-3 / 1e-2."""
+    stated = {("bf16", False): 1e-2, ("bf16", True): 1e-1, ("f16", False): 2e-3, ("f16", True): 1e-2}
+    for (dtype, smooth), bound in stated.items():
+        c, sc, q, qt, got, _ = _run_lowp(256, 32, 16, dtype, smooth)
+        ref = oracle.tendencies(*q, c)
+        for x, r in zip(got, ref):
+            rel = np.abs(interior(x) - interior(r)).max() / np.abs(interior(r)).max()
+            assert rel <= bound, (dtype, smooth, rel)

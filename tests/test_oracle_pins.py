@@ -191,3 +191,29 @@ def test_step_adjoint_matches_central_differences():
     fd = (loss(u + eps * d[0], v + eps * d[1], w + eps * d[2])
           - loss(u - eps * d[0], v - eps * d[1], w - eps * d[2])) / (2 * eps)
     assert abs(fd - ana) <= 1e-7 * abs(ana)
+
+
+def test_abs_terms_bounds_and_pins():
+    nx, ny, nz = 8, 6, 7
+    c = inputs.make_coeffs(nz, anelastic=True)
+    u, v, w = (f.numpy().astype(np.float64) for f in inputs.random_fields(nx, ny, nz))
+    s = tend64(u, v, w, c)
+    a = oracle.abs_terms(u, v, w, c)
+    for si, ai in zip(s, a):
+        assert np.all(ai >= np.abs(si) * (1 - 1e-15))        # triangle inequality
+    a2 = oracle.abs_terms(2 * u, 2 * v, 2 * w, c)
+    for x, y in zip(a, a2):
+        assert np.array_equal(4 * x, y)
+    # single nonzero term: u only at (k,j,i-1) and (k,j,i) -> su(k,j,i) has the
+    # one x-term tcx*u(i-1)*(u+u(i-1)) with b, d of one sign: equality
+    z = np.zeros_like(u)
+    uu = z.copy()
+    uu[3, 3, 3] = 1.5
+    uu[3, 3, 4] = 0.5
+    s1 = tend64(uu, z, z, c)
+    a1 = oracle.abs_terms(uu, z, z, c)
+    assert s1[0][3, 3, 4] != 0 and a1[0][3, 3, 4] == abs(s1[0][3, 3, 4])
+    # the FP32 oracle's rounding error sits inside a small multiple of u32 * sum
+    s32 = tend32(u, v, w, c)
+    for x, y, ai in zip(s32, s, a):
+        assert np.all(np.abs(x - y) <= 16 * 2.0 ** -24 * ai + 1e-300)
