@@ -180,6 +180,30 @@ pw_status_t pw_error_norms(pw_handle_t h, const void *test, float scale, const d
 pw_status_t pw_weighted_dot(pw_handle_t h, const void *a, float sa, const void *b, float sb,
                             const double *wk, int32_t k0, int32_t k1, double *out, pw_stream_t stream);
 
+/*
+ * pw_weighted_dot without any device allocation (the paper has no
+ * counterpart; this is a service for callers).  Same arguments, result and
+ * synchronisation as pw_weighted_dot, but the per-block partials, the result
+ * and the copied level weights live in one statically allocated device array
+ * of 64.8 KB that every device loading the library holds until the process
+ * exits, instead of scratch the handle allocates on first use.  For callers
+ * that cannot call cudaMalloc once their run has started (a host model that
+ * owns the device memory budget through its own allocator, or a time loop
+ * that must not meet an allocation failure): create the handle at start-up,
+ * then this call allocates nothing, neither cudaMalloc nor cudaFree nor any
+ * allocating library routine.
+ * Limit: nz + 2 <= 4096 levels; larger grids get PW_ERR_UNSUPPORTED (use
+ * pw_weighted_dot).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (every call overwrites what it reads, so nothing needs
+ * clearing): calls that overlap on the GPU, on different streams or host
+ * threads, race on it and must be serialised by the caller.
+ */
+pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void *a, float sa, const void *b, float sb,
+                                    const double *wk, int32_t k0, int32_t k1, double *out,
+                                    pw_stream_t stream);
+
 /* Wait for `stream`, then report (and clear) any bounded-wait timeout a
  * kernel of this handle recorded, and any pending CUDA error. */
 pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream);

@@ -199,6 +199,29 @@ static void make_scales(const float* scale, Scales* sc, bool* scaled) {
     }
 }
 
+namespace pw {
+
+pw_status_t internal_fail(pw_status_t s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+pw_status_t internal_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms) {
+    if (!h) return false;
+    *g = h->grid;
+    *num_sms = h->num_sms;
+    return true;
+}
+
+}  // namespace pw
+
 extern "C" {
 
 pw_status_t pw_grid_default(int32_t nx, int32_t ny, int32_t nz, int32_t halo, pw_dtype_t dtype, pw_grid_t* out,

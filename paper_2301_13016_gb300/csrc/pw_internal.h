@@ -70,4 +70,10 @@ cudaError_t launch_error_norms(pw_dtype_t dt, const GridDev& g, const void* t, f
 cudaError_t launch_weighted_dot(pw_dtype_t dt, const GridDev& g, const void* a, float sa, const void* b, float sb,
                                 const double* wk, int k0, int k1, double* scratch, int nblocks, cudaStream_t s);
 
+// Error reporting and handle access for translation units other than
+// pw_api.cu (set the thread-local message pw_last_error returns).
+pw_status_t internal_fail(pw_status_t s, const char* fmt, ...);
+pw_status_t internal_cuda_fail(cudaError_t e, const char* what);
+bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
+
 }  // namespace pw

@@ -57,6 +57,8 @@ SIGNATURES = [
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
     ("pw_error_norms", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32, _dp, _VP]),
+    ("pw_weighted_dot_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32,
+                                               _dp, _VP]),
     ("pw_sync", ctypes.c_int, [_VP, _VP]),
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
     ("pw_last_error", ctypes.c_char_p, []),
@@ -278,6 +280,23 @@ class PW:
     def selftest_wait_timeout(self, limit_ns=100_000_000, stream=None):
         _check(lib().pw_selftest_wait_timeout(self.h, int(limit_ns), _stream_ptr(stream)),
                "pw_selftest_wait_timeout")
+
+    def weighted_dot_noalloc(self, a, b, wk=None, k0=1, k1=None, sa=1.0, sb=1.0, stream=None):
+        """weighted_dot with its scratch in the library's static device array:
+        no device allocation at call time (see pw_weighted_dot_noalloc)."""
+        g = self.grid
+        k1 = g.nz if k1 is None else k1
+        wp = None
+        if wk is not None:
+            wk = np.ascontiguousarray(wk, dtype=np.float64)
+            if wk.shape != (g.nz + 2,):
+                raise ValueError("wk must have nz+2 entries")
+            wp = wk.ctypes.data_as(_dp)
+        out = ctypes.c_double()
+        _check(lib().pw_weighted_dot_noalloc(self.h, _ptr(a, g, "a"), float(sa), _ptr(b, g, "b"), float(sb), wp,
+                                             int(k0), int(k1), ctypes.byref(out), _stream_ptr(stream)),
+               "pw_weighted_dot_noalloc")
+        return float(out.value)
 
     def sync(self, stream=None):
         _check(lib().pw_sync(self.h, _stream_ptr(stream)), "pw_sync")
