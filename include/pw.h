@@ -150,6 +150,25 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
                                void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
 
 /*
+ * Advance the advection-only system nsteps forward-Euler steps,
+ * q <- q + dt * s(q) for q = (u, v, w), with s the PW source terms (the scheme
+ * is evaluated every model timestep, Sec. 2.2), doubly periodic lateral
+ * boundaries and the rigid surface and lid (s is zero there, so those levels
+ * keep their values).  On entry the interior of (u, v, w) is the state and
+ * its halos are ignored; on return (u, v, w) hold the state after nsteps
+ * steps with periodic halos filled.  tmp_u, tmp_v, tmp_w are caller-owned
+ * scratch fields of the same layout (contents overwritten).  Each step is one
+ * fused kernel pass that reads the state once and writes the next state once,
+ * periodic images of the boundary cells included; the two buffer sets
+ * alternate, and an odd nsteps ends with a device copy back into (u, v, w).
+ * scale: NULL or 3 floats {s_u, s_v, s_w}: physical = stored * s (for 16-bit
+ * storage; the state is rounded to the storage type after every step).
+ * All six pointers must be distinct.  nsteps = 0 only refreshes the halos.
+ */
+pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void *tmp_v, void *tmp_w,
+                    float dt, int32_t nsteps, const float *scale, pw_stream_t stream);
+
+/*
  * Periodic lateral boundary: copy interior values into the lateral halo of
  * f (all halo columns and rows, corners included, levels k = 1..nz), as the
  * halo swap of a doubly periodic domain before each evaluation of the scheme

@@ -14,10 +14,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpw.so")
-SOURCES = ["pw_api.cu", "pw_tend.cu", "pw_halo.cu", "pw_norms.cu", "pw_selftest.cu", "pw_noalloc.cu"]
+SOURCES = ["pw_api.cu", "pw_tend.cu", "pw_step.cu", "pw_halo.cu", "pw_norms.cu", "pw_selftest.cu", "pw_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
     [os.path.join(ROOT, "include", "pw.h")]
 NVCC = os.environ.get("NVCC", "nvcc")
+EXTRA = os.environ.get("PW_NVCC_EXTRA", "").split()     # e.g. kernel knobs -DPW_TMA_UNROLL=0
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
@@ -34,7 +35,7 @@ def _compile(src, verbose):
     deps = [os.path.join(CSRC, src)] + HEADERS
     if not _stale(obj, deps):
         return obj, ""
-    cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [NVCC] + FLAGS + EXTRA + (["-Xptxas", "-v"] if verbose else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

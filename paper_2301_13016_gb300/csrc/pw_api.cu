@@ -77,7 +77,8 @@ struct pw_handle_s {
     int last_kernel = 0;
     TmaConfig tma_user{0, 0, 0};
     TmaConfig tma_auto{0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
-    MapCacheEntry maps[3];
+    MapCacheEntry maps[8];
+    int map_next = 0;   // round-robin replacement
     // pw_tendencies_host staging
     void* d_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // validation scratch: 4*(nblocks+1) doubles + wk (nz+2 doubles)
@@ -139,12 +140,14 @@ static bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static pw_status_t encode_map(pw_handle_t h, int slot, const void* ptr, int ox, int ty, CUtensorMap* out) {
-    MapCacheEntry& e = h->maps[slot];
-    if (e.ptr == ptr && e.ty == ty) {
-        *out = e.map;
-        return PW_OK;
-    }
+static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int ty, CUtensorMap* out) {
+    for (auto& c : h->maps)
+        if (c.ptr == ptr && c.ty == ty) {
+            *out = c.map;
+            return PW_OK;
+        }
+    MapCacheEntry& e = h->maps[h->map_next];
+    h->map_next = (h->map_next + 1) % (int)(sizeof(h->maps) / sizeof(h->maps[0]));
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const pw_grid_t& g = h->grid;
@@ -167,12 +170,13 @@ static pw_status_t encode_map(pw_handle_t h, int slot, const void* ptr, int ox, 
     return PW_OK;
 }
 
-// Launch shape of the TMA kernel: user overrides, else ty = 8, 4 stages, and
+// Launch shape of the TMA kernel: user overrides, else ty = 4 rows, 4 stages
+// (the fastest measured shape on GB300 for FP32 and 16-bit storage), and
 // enough k segments for about two waves of CTAs over the SMs.
 static TmaConfig choose_tma(pw_handle_t h) {
     if (h->tma_auto.ty) return h->tma_auto;
     TmaConfig c;
-    c.ty = h->tma_user.ty ? h->tma_user.ty : 8;
+    c.ty = h->tma_user.ty ? h->tma_user.ty : 4;
     c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
     if (h->tma_user.nseg) {
         c.nseg = h->tma_user.nseg;
@@ -302,7 +306,7 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind) {
 pw_status_t pw_set_tma_config(pw_handle_t h, int32_t ty, int32_t stages, int32_t nseg) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
-    TmaConfig c{ty ? ty : 8, stages ? stages : 4, 1};
+    TmaConfig c{ty ? ty : 4, stages ? stages : 4, 1};
     if (!tma_config_supported(h->grid.dtype, c))
         return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for ty=%d stages=%d", c.ty, c.stages);
     h->tma_user = TmaConfig{ty, stages, nseg};
@@ -348,7 +352,7 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         TmaConfig c = choose_tma(h);
         CUtensorMap maps[3];
         for (int q = 0; q < 3; ++q) {
-            pw_status_t st = encode_map(h, q, ins[q], ox, c.ty, &maps[q]);
+            pw_status_t st = encode_map(h, ins[q], ox, c.ty, &maps[q]);
             if (st != PW_OK) return st;
         }
         cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, scaled, cf, h->d_err, c, s);
@@ -394,6 +398,83 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len, cudaMemcpyDeviceToHost, s),
                 "pw_tendencies_host output copy");
     PW_CUDA(cudaStreamSynchronize(s), "pw_tendencies_host synchronize");
+    return PW_OK;
+}
+
+pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void* tmp_v, void* tmp_w, float dt,
+                    int32_t nsteps, const float* scale, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    void* bufs[6] = {u, v, w, tmp_u, tmp_v, tmp_w};
+    for (int a = 0; a < 6; ++a) {
+        if (!bufs[a]) return fail(PW_ERR_ARG, "a field pointer is NULL");
+        for (int b = 0; b < a; ++b)
+            if (bufs[a] == bufs[b]) return fail(PW_ERR_ARG, "state and scratch buffers must be distinct");
+    }
+    if (nsteps < 0) return fail(PW_ERR_ARG, "nsteps must be >= 0");
+    if (!(dt == dt) || dt > 3.0e38f || dt < -3.0e38f) return fail(PW_ERR_ARG, "dt must be finite");
+    Scales sc;
+    bool scaled = false;
+    for (int q = 0; q < 3; ++q) {
+        const float x = scale ? scale[q] : 1.f;
+        if (!(x > 0.f) || !(x < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
+        sc.in[q] = x;
+        sc.out[q] = 1.f / x;   // the next state is stored with the same scale
+        if (x != 1.f) scaled = true;
+    }
+    const GridDev g = to_dev(h->grid);
+    CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const pw_dtype_t dtp = h->grid.dtype;
+    for (int q = 0; q < 3; ++q) {
+        cudaError_t e = launch_fill_halo(dtp, g, bufs[q], h->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
+    }
+    int ox = 0;
+    const char* why = "";
+    const bool layout_ok = tma_layout_ok(h->grid, &ox, &why);
+    bool ptrs_ok = true;
+    for (auto p : bufs) ptrs_ok = ptrs_ok && aligned16(p);
+    if (h->kernel_kind == 2) {
+        if (!layout_ok) return fail(PW_ERR_UNSUPPORTED, "TMA kernel requested but %s", why);
+        if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
+    }
+    const bool use_tma = (h->kernel_kind == 2) || (h->kernel_kind == 0 && layout_ok && ptrs_ok);
+    TmaConfig c{};
+    if (use_tma) c = choose_tma(h);
+    for (int n = 0; n < nsteps; ++n) {
+        void** src = (n % 2 == 0) ? bufs : bufs + 3;
+        void** dst = (n % 2 == 0) ? bufs + 3 : bufs;
+        cudaError_t e;
+        if (use_tma) {
+            CUtensorMap maps[3];
+            for (int q = 0; q < 3; ++q) {
+                pw_status_t st = encode_map(h, src[q], ox, c.ty, &maps[q]);
+                if (st != PW_OK) return st;
+            }
+            e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);
+        } else {
+            e = launch_step_generic(dtp, g, src[0], src[1], src[2], dst[0], dst[1], dst[2], sc, scaled, cf, dt,
+                                    h->num_sms, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        if (g.halo != 1)   // the kernel writes the images of a one-cell halo only
+            for (int q = 0; q < 3; ++q) {
+                e = launch_fill_halo(dtp, g, dst[q], h->num_sms, s);
+                if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
+            }
+    }
+    h->last_kernel = use_tma ? 2 : 1;
+    if (nsteps % 2 == 1) {   // the last state is in the scratch buffers: copy levels 1..nz back
+        const size_t es = dtype_size(dtp);
+        const pw_grid_t& gg = h->grid;
+        const size_t lo = (size_t)(gg.origin + gg.pitch_k + (long long)(1 - gg.halo) * gg.pitch_j + 1 - gg.halo);
+        const size_t hi = (size_t)(gg.origin + (long long)gg.nz * gg.pitch_k +
+                                   (long long)(gg.ny + gg.halo) * gg.pitch_j + gg.nx + gg.halo + 1);
+        for (int q = 0; q < 3; ++q)
+            PW_CUDA(cudaMemcpyAsync((char*)bufs[q] + lo * es, (const char*)bufs[3 + q] + lo * es, (hi - lo) * es,
+                                    cudaMemcpyDeviceToDevice, s),
+                    "state copy");
+    }
     return PW_OK;
 }
 

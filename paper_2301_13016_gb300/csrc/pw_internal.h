@@ -54,6 +54,15 @@ cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUten
                             void* su, void* sv, void* sw, const Scales& sc, bool scaled, const CoefDev& cf,
                             int* err, const TmaConfig& c, cudaStream_t s);
 
+// Forward-Euler step kernels: (nu, nv, nw) = (u, v, w) + tstep * s(u, v, w),
+// interior levels 1..nz plus the periodic images of boundary cells (halo 1).
+cudaError_t launch_step_generic(pw_dtype_t dt, const GridDev& g, const void* u, const void* v, const void* w,
+                                void* nu, void* nv, void* nw, const Scales& sc, bool scaled, const CoefDev& cf,
+                                float tstep, int num_sms, cudaStream_t s);
+cudaError_t launch_step_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
+                            void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                            const TmaConfig& c, cudaStream_t s);
+
 // Blocks of the TMA kernel resident per SM for a config (0 if it cannot launch).
 int tma_blocks_per_sm(pw_dtype_t dt, const TmaConfig& c);
 

@@ -1,0 +1,539 @@
+// PW stencil kernels (Sec. 2.2; per-cell arithmetic shape Sec. 4), templated
+// on the storage type T and on what the epilogue does with the source terms:
+//   MODE_TEND: store su, sv, sw;
+//   MODE_STEP: store the forward-Euler update q + dt*s of u, v, w, together
+//              with the periodic images of the boundary cells (halo 1), so the
+//              next step reads a complete halo.
+// Instantiated by pw_tend.cu (MODE_TEND) and pw_step.cu (MODE_STEP).
+#pragma once
+
+#include "pw_device.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+enum { MODE_TEND = 0, MODE_STEP = 1 };
+
+// Writes the three outputs of one cell or one row vector of 4 cells, plus the
+// periodic images (MODE_STEP, halo 1) when the cells lie on the lateral
+// boundary.  o = offset of (k, j, i0); cells i0..i0+n-1.
+template <typename T, int MODE>
+struct Epilogue;
+
+template <typename T>
+struct Epilogue<T, MODE_TEND> {
+    static __device__ __forceinline__ void store1(T* o0, T* o1, T* o2, long long o, float a, float b, float c,
+                                                  const GridDev&, int, int) {
+        o0[o] = Store<T>::from_f(a);
+        o1[o] = Store<T>::from_f(b);
+        o2[o] = Store<T>::from_f(c);
+    }
+    static __device__ __forceinline__ void store4v(T* o0, T* o1, T* o2, long long o, const float (&a)[4],
+                                                   const float (&b)[4], const float (&c)[4], const GridDev&, int,
+                                                   int) {
+        store4(o0 + o, a);
+        store4(o1 + o, b);
+        store4(o2 + o, c);
+    }
+};
+
+template <typename T>
+struct Epilogue<T, MODE_STEP> {
+    // one cell (j, i) at offset o
+    static __device__ __forceinline__ void store1(T* o0, T* o1, T* o2, long long o, float a, float b, float c,
+                                                  const GridDev& g, int j, int i) {
+        const T ta = Store<T>::from_f(a), tb = Store<T>::from_f(b), tc = Store<T>::from_f(c);
+        auto put = [&](long long p) {
+            o0[p] = ta;
+            o1[p] = tb;
+            o2[p] = tc;
+        };
+        put(o);
+        if (g.halo != 1) return;   // deeper halos are refreshed by the halo kernel
+        const long long dxp = (i == 1) ? (long long)g.nx : 0;        // image at i = nx+1
+        const long long dxm = (i == g.nx) ? -(long long)g.nx : 0;    // image at i = 0
+        const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
+        const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
+        if (dxp) put(o + dxp);
+        if (dxm) put(o + dxm);
+        if (dyp) {
+            put(o + dyp);
+            if (dxp) put(o + dyp + dxp);
+            if (dxm) put(o + dyp + dxm);
+        }
+        if (dym) {
+            put(o + dym);
+            if (dxp) put(o + dym + dxp);
+            if (dxm) put(o + dym + dxm);
+        }
+    }
+    // a vector of 4 cells (j, i0..i0+3), i0 = 1 mod 4, nx = 0 mod 4
+    static __device__ __forceinline__ void store4v(T* o0, T* o1, T* o2, long long o, const float (&a)[4],
+                                                   const float (&b)[4], const float (&c)[4], const GridDev& g, int j,
+                                                   int i0) {
+        store4(o0 + o, a);
+        store4(o1 + o, b);
+        store4(o2 + o, c);
+        if (g.halo != 1) return;
+        const bool west = (i0 == 1), east = (i0 + 3 == g.nx);
+        const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
+        const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
+        auto row = [&](long long p) {   // the row image plus its corner images
+            store4(o0 + p, a);
+            store4(o1 + p, b);
+            store4(o2 + p, c);
+        };
+        auto cell = [&](long long p, int q) {
+            o0[p] = Store<T>::from_f(a[q]);
+            o1[p] = Store<T>::from_f(b[q]);
+            o2[p] = Store<T>::from_f(c[q]);
+        };
+        const long long shifts[3] = {0, dyp, dym};
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (s > 0 && shifts[s] == 0) continue;
+            const long long p = o + shifts[s];
+            if (s > 0) row(p);
+            if (west) cell(p + g.nx, 0);            // cell i = 1 -> i = nx+1
+            if (east) cell(p + 3 - g.nx, 3);        // cell i = nx (offset +3) -> i = 0
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Generic kernel: one thread per cell, plain loads, any layout and alignment.
+template <typename T, bool SCALED, int MODE>
+__global__ void generic_kernel(const GridDev g, const T* __restrict__ u, const T* __restrict__ v,
+                               const T* __restrict__ w, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2,
+                               const Scales sc, const CoefDev cf, const float dt) {
+    const long long nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long total = nx * ny * nz;
+    const int nzp2 = g.nz + 2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(idx % nx);
+        const int j = 1 + (int)((idx / nx) % ny);
+        const int k = 1 + (int)(idx / (nx * ny));
+        const long long c = g.origin + k * g.pk + j * g.pj + i;
+        auto at = [&](const T* f, int dk, int dj, int di, float s) {
+            float x = Store<T>::to_f(f[c + dk * g.pk + dj * g.pj + di]);
+            return SCALED ? x * s : x;
+        };
+        auto U = [&](int dk, int dj, int di) { return at(u, dk, dj, di, sc.in[0]); };
+        auto V = [&](int dk, int dj, int di) { return at(v, dk, dj, di, sc.in[1]); };
+        auto W = [&](int dk, int dj, int di) { return at(w, dk, dj, di, sc.in[2]); };
+        float ru = 0.f, rv = 0.f, rw = 0.f;
+        if (k >= 2) {
+            const float tz1 = cf.tz[k], tz2 = cf.tz[nzp2 + k];
+            const bool top = k < g.nz;
+            ru = cf.tcx * (U(0, 0, -1) * (U(0, 0, 0) + U(0, 0, -1)) - U(0, 0, 1) * (U(0, 0, 0) + U(0, 0, 1))) +
+                 cf.tcy * (U(0, -1, 0) * (V(0, -1, 0) + V(0, -1, 1)) - U(0, 1, 0) * (V(0, 0, 0) + V(0, 0, 1))) +
+                 tz1 * (U(-1, 0, 0) * (W(-1, 0, 0) + W(-1, 0, 1)));
+            rv = cf.tcx * (V(0, 0, -1) * (U(0, 0, -1) + U(0, 1, -1)) - V(0, 0, 1) * (U(0, 0, 0) + U(0, 1, 0))) +
+                 cf.tcy * (V(0, -1, 0) * (V(0, 0, 0) + V(0, -1, 0)) - V(0, 1, 0) * (V(0, 0, 0) + V(0, 1, 0))) +
+                 tz1 * (V(-1, 0, 0) * (W(-1, 0, 0) + W(-1, 1, 0)));
+            if (top) {
+                ru -= tz2 * (U(1, 0, 0) * (W(0, 0, 0) + W(0, 0, 1)));
+                rv -= tz2 * (V(1, 0, 0) * (W(0, 0, 0) + W(0, 1, 0)));
+                const float td1 = cf.tz[2 * nzp2 + k], td2 = cf.tz[3 * nzp2 + k];
+                rw = cf.tcx * (W(0, 0, -1) * (U(0, 0, -1) + U(1, 0, -1)) - W(0, 0, 1) * (U(0, 0, 0) + U(1, 0, 0))) +
+                     cf.tcy * (W(0, -1, 0) * (V(0, -1, 0) + V(1, -1, 0)) - W(0, 1, 0) * (V(0, 0, 0) + V(1, 0, 0))) +
+                     (td1 * (W(-1, 0, 0) * (W(0, 0, 0) + W(-1, 0, 0))) - td2 * (W(1, 0, 0) * (W(0, 0, 0) + W(1, 0, 0))));
+            }
+        }
+        if (MODE == MODE_STEP) {
+            ru = fmaf(dt, ru, U(0, 0, 0));
+            rv = fmaf(dt, rv, V(0, 0, 0));
+            rw = fmaf(dt, rw, W(0, 0, 0));
+        }
+        if (SCALED) {
+            ru *= sc.out[0];
+            rv *= sc.out[1];
+            rw *= sc.out[2];
+        }
+        Epilogue<T, MODE>::store1(o0, o1, o2, c, ru, rv, rw, g, j, i);
+    }
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_generic_mode(const GridDev& g, const void* u, const void* v, const void* w, void* o0,
+                                       void* o1, void* o2, const Scales& sc, bool scaled, const CoefDev& cf,
+                                       float dt, int num_sms, cudaStream_t s) {
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    const int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    const long long cap = (long long)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (scaled)
+        generic_kernel<T, true, MODE><<<(unsigned)blocks, threads, 0, s>>>(
+            g, (const T*)u, (const T*)v, (const T*)w, (T*)o0, (T*)o1, (T*)o2, sc, cf, dt);
+    else
+        generic_kernel<T, false, MODE><<<(unsigned)blocks, threads, 0, s>>>(
+            g, (const T*)u, (const T*)v, (const T*)w, (T*)o0, (T*)o1, (T*)o2, sc, cf, dt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// TMA k-march kernel.
+//
+// A CTA owns an x-y tile of 128 x TY interior columns and one k segment, and
+// marches up the column one level at a time.  Level planes of u, v, w (the
+// tile plus a one-cell halo, widened in x to the 16-byte TMA granule) arrive
+// in a ring of S shared-memory stages by 3D TMA box copies that one thread
+// issues, each stage completing on its own mbarrier; S-1 planes are in flight
+// ahead of the level being computed, so every input element is read from HBM
+// once and the copy engine, not the warps, keeps bytes in flight.
+//
+// Thread (lane, ty) computes 4 consecutive cells along x of row ty.  Shared
+// memory rows are read as 16-byte (FP32) or 8-byte (16-bit) vectors; x
+// neighbours come from the adjacent lanes by warp shuffles (the two
+// tile-edge lanes read theirs from the halo columns); y neighbours from the
+// rows above and below.  Registers carry from one level to the next: the
+// level-k+1 rows the upper terms read (they are the level-k rows of the next
+// step), the level k-1 values at the cell (a rolling window in z), and the
+// three vertical pair sums of the upper fluxes, which are the lower pair sums
+// of the next level.  Pair sums along x are shared by neighbouring cells of a
+// thread.  Outputs go straight from registers to HBM as full vectors.
+template <typename T, int TY, int S>
+struct TmaLayout {
+    static constexpr int TX = 128;
+    static constexpr int PADX = 16 / (int)sizeof(T);   // elements in one 16-byte granule
+    static constexpr int BW = TX + 2 * PADX;           // box width
+    static constexpr int ROWS = TY + 2;
+    static constexpr int FIELD_RAW = BW * ROWS;
+    static constexpr int FIELD_BYTES = ((FIELD_RAW * (int)sizeof(T) + 127) / 128) * 128;
+    static constexpr int FIELD = FIELD_BYTES / (int)sizeof(T);
+    static constexpr int STAGE = 3 * FIELD;
+    static constexpr uint32_t TX_BYTES = 3u * FIELD_RAW * (uint32_t)sizeof(T);
+    static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16;
+};
+
+// Build-time knobs of the k-march kernel (defaults are the measured best):
+// PW_TMA_UNROLL   1 = march in blocks of S levels with compile-time ring
+//                 slots, 0 = one level per loop trip;
+// PW_TMA_MAX_MINB cap on the resident CTAs per SM the register budget is
+//                 sized for.
+#ifndef PW_TMA_UNROLL
+#define PW_TMA_UNROLL 0
+#endif
+#ifndef PW_TMA_MAX_MINB
+#define PW_TMA_MAX_MINB 2
+#endif
+
+// Resident CTAs per SM the register budget is sized for: what shared memory
+// and the thread limit allow, at most PW_TMA_MAX_MINB.
+template <typename T, int TY, int S>
+constexpr int tma_min_blocks() {
+    constexpr int by_smem = (int)((227u * 1024u) / TmaLayout<T, TY, S>::SMEM);
+    constexpr int by_threads = 2048 / (32 * TY);
+    constexpr int m = by_smem < by_threads ? by_smem : by_threads;
+    return m < 1 ? 1 : (m > PW_TMA_MAX_MINB ? PW_TMA_MAX_MINB : m);
+}
+
+template <typename T, int TY, int S, bool SCALED, int MODE>
+__global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
+    tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
+               const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
+               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const Scales sc,
+               const CoefDev cf, const float dt, int* __restrict__ err) {
+    using L = TmaLayout<T, TY, S>;
+    constexpr int BW = L::BW;
+    constexpr int PADX = L::PADX;
+    constexpr int FU = 0, FV = L::FIELD, FW = 2 * L::FIELD;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* stages = reinterpret_cast<T*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * L::STAGE * sizeof(T));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S);
+
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + lane;
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    const int nz = g.nz;
+    const int kb = 1 + (int)(((long long)bz * nz) / nseg);
+    const int ke = (int)(((long long)(bz + 1) * nz) / nseg);
+    const int pb = max(kb - 1, 1);
+    const int pe = min(ke + 1, nz);
+    const int np = pe - pb + 1;
+    if (ke < kb) return;   // empty k segment (the host never launches one)
+
+    const int X0 = ox + 1 + L::TX * bx - PADX;
+    const int Y0 = TY * by + g.halo - 1;
+
+    auto issue = [&](int p) {   // plane pb+p into stage p % S
+        const int s = p % S;
+        T* dst = stages + s * L::STAGE;
+        mbar_arrive_expect_tx(&bars[s], L::TX_BYTES);
+        tma_load_3d(dst + FU, &tm_u, X0, Y0, pb + p, &bars[s]);
+        tma_load_3d(dst + FV, &tm_v, X0, Y0, pb + p, &bars[s]);
+        tma_load_3d(dst + FW, &tm_w, X0, Y0, pb + p, &bars[s]);
+    };
+
+    int issued = 0;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        prefetch_tensormap(&tm_u);
+        prefetch_tensormap(&tm_v);
+        prefetch_tensormap(&tm_w);
+        for (; issued < S && issued < np; ++issued) issue(issued);
+    }
+
+    const int r = ty + 1;
+    const int c0 = 4 * lane + PADX;
+    // tile-edge neighbour column: lane 0 needs x = -1, lane 31 needs x = 128;
+    // the other lanes read lane 31's address (a broadcast, no bank conflict)
+    const int ce = (lane == 0) ? PADX - 1 : L::TX + PADX;
+    const int j = TY * by + 1 + ty;
+    const int i0 = 1 + L::TX * bx + 4 * lane;
+    const bool valid = (j <= g.ny) && (i0 <= g.nx);
+    const long long row_off = g.origin + (long long)j * g.pj + i0;
+    const float tcx = cf.tcx, tcy = cf.tcy;
+    const int nzp2 = nz + 2;
+    const unsigned FULL = 0xffffffffu;
+    const float su_in = sc.in[0], sv_in = sc.in[1], sw_in = sc.in[2];
+
+    auto ld = [&](const T* p, float (&o)[4], float s) {
+        load4(p, o);
+        if (SCALED) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] *= s;
+        }
+    };
+    auto ld1 = [&](const T* p, float s) {
+        float x = Store<T>::to_f(*p);
+        return SCALED ? x * s : x;
+    };
+    // x-neighbours of a row vector: value at x = -1 (m) and x = 4 (p)
+    auto nbr_m = [&](const float (&x)[4], float edge) {
+        float m = __shfl_up_sync(FULL, x[3], 1);
+        return lane == 0 ? edge : m;
+    };
+    auto nbr_p = [&](const float (&x)[4], float edge) {
+        float p = __shfl_down_sync(FULL, x[0], 1);
+        return lane == 31 ? edge : p;
+    };
+
+    // rows of level kk carried from the previous step (loaded there as level kk+1)
+    float u0[4], v0[4], vs[4], w0[4];
+    // level kk-1 at the cell, and the lower vertical pair sums of level kk
+    float ud[4], vd[4], wd[4], pzu[4], pzv[4], pzw[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        ud[c] = vd[c] = wd[c] = pzu[c] = pzv[c] = pzw[c] = 0.f;
+        u0[c] = v0[c] = vs[c] = w0[c] = 0.f;
+    }
+    int waited = 0;   // planes 0..waited-1 are known complete
+    bool aborted = false;
+
+    // One level of the march.  stg / stg_up: ring slots of levels kk and kk+1;
+    // par_up: phase parity of level kk+1's slot.  Returns false on abort.
+    auto level = [&](const int kk, const int stg, const int stg_up, const uint32_t par_up) -> bool {
+        const int lp = kk - pb;
+        bool ok = true;
+        if (lp == 0) ok = mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);
+        const bool have_up = (kk + 1 <= pe);
+        if (ok && have_up) ok = mbar_wait_bounded(&bars[stg_up], par_up, kWaitLimitNs);
+        ok = __all_sync(FULL, ok);
+        if (!ok) *abort_flag = 1;
+        if (ok) {
+            waited = lp + (have_up ? 2 : 1);
+            const T* P = stages + stg * L::STAGE;   // level kk
+            if (lp == 0) {
+                ld(P + FU + r * BW + c0, u0, su_in);
+                ld(P + FV + r * BW + c0, v0, sv_in);
+                ld(P + FV + (r - 1) * BW + c0, vs, sv_in);
+                ld(P + FW + r * BW + c0, w0, sw_in);
+            }
+            float wn[4];
+            ld(P + FW + (r + 1) * BW + c0, wn, sw_in);
+            const float ew = ld1(P + FW + r * BW + ce, sw_in);
+            const float w0m = nbr_m(w0, ew), w0p = nbr_p(w0, ew);
+            const float W[6] = {w0m, w0[0], w0[1], w0[2], w0[3], w0p};   // x = -1..4
+
+            // level kk+1 rows (upper terms; carried into the next step)
+            float uu[4] = {0, 0, 0, 0}, vu[4] = {0, 0, 0, 0}, vus[4] = {0, 0, 0, 0}, wu[4] = {0, 0, 0, 0};
+            float euu = 0.f;
+            if (have_up) {
+                const T* Q = stages + stg_up * L::STAGE;
+                ld(Q + FU + r * BW + c0, uu, su_in);
+                ld(Q + FV + r * BW + c0, vu, sv_in);
+                ld(Q + FV + (r - 1) * BW + c0, vus, sv_in);
+                ld(Q + FW + r * BW + c0, wu, sw_in);
+                euu = ld1(Q + FU + r * BW + ce, su_in);
+            }
+            // upper vertical pair sums of level kk = lower ones of level kk+1
+            float pzu_n[4], pzv_n[4], pzw_n[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pzu_n[c] = W[c + 1] + W[c + 2];   // w(k,i) + w(k,i+1)
+                pzv_n[c] = w0[c] + wn[c];         // w(k,j) + w(k,j+1)
+                pzw_n[c] = w0[c] + wu[c];         // w(k) + w(k+1)
+            }
+
+            const bool compute = (kk >= kb) && (kk >= 2);
+            float ru[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, rw[4] = {0, 0, 0, 0};
+            if (compute) {
+                float us[4], un[4], vn[4], ws[4];
+                ld(P + FU + (r - 1) * BW + c0, us, su_in);
+                ld(P + FU + (r + 1) * BW + c0, un, su_in);
+                ld(P + FV + (r + 1) * BW + c0, vn, sv_in);
+                ld(P + FW + (r - 1) * BW + c0, ws, sw_in);
+                const float eu = ld1(P + FU + r * BW + ce, su_in);
+                const float ev = ld1(P + FV + r * BW + ce, sv_in);
+                const float eun = ld1(P + FU + (r + 1) * BW + ce, su_in);
+                const float evs = ld1(P + FV + (r - 1) * BW + ce, sv_in);
+                const float U[6] = {nbr_m(u0, eu), u0[0], u0[1], u0[2], u0[3], nbr_p(u0, eu)};
+                const float V[6] = {nbr_m(v0, ev), v0[0], v0[1], v0[2], v0[3], nbr_p(v0, ev)};
+                const float UN[5] = {nbr_m(un, eun), un[0], un[1], un[2], un[3]};   // x = -1..3
+                const float VS[5] = {vs[0], vs[1], vs[2], vs[3], nbr_p(vs, evs)};   // x = 0..4
+                const float UU[5] = {nbr_m(uu, euu), uu[0], uu[1], uu[2], uu[3]};   // x = -1..3
+
+                // pair sums along x shared by neighbouring cells: index c is the
+                // pair (x = c-1, c)
+                float pxu[5], qx[5], rx[5], pxv[4], pys[4];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    pxu[c] = U[c] + U[c + 1];     // u(i-1) + u(i)
+                    qx[c] = U[c] + UN[c];         // u(j,i-1) + u(j+1,i-1)
+                    rx[c] = U[c] + UU[c];         // u(k,i-1) + u(k+1,i-1)
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    pxv[c] = V[c + 1] + V[c + 2];  // v(j,i) + v(j,i+1)
+                    pys[c] = VS[c] + VS[c + 1];    // v(j-1,i) + v(j-1,i+1)
+                }
+                const float tz1 = __ldg(cf.tz + kk);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    // su
+                    float x = tcx * fmaf(-U[c + 2], pxu[c + 1], U[c] * pxu[c]);
+                    x = fmaf(tcy, fmaf(-un[c], pxv[c], us[c] * pys[c]), x);
+                    ru[c] = fmaf(tz1, ud[c] * pzu[c], x);
+                    // sv
+                    float y = tcx * fmaf(-V[c + 2], qx[c + 1], V[c] * qx[c]);
+                    y = fmaf(tcy, fmaf(-vn[c], V[c + 1] + vn[c], vs[c] * (V[c + 1] + vs[c])), y);
+                    rv[c] = fmaf(tz1, vd[c] * pzv[c], y);
+                }
+                if (have_up) {   // kk < nz: upper vertical fluxes and sw
+                    const float tz2 = __ldg(cf.tz + nzp2 + kk);
+                    const float td1 = __ldg(cf.tz + 2 * nzp2 + kk);
+                    const float td2 = __ldg(cf.tz + 3 * nzp2 + kk);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        ru[c] = fmaf(-tz2, uu[c] * pzu_n[c], ru[c]);
+                        rv[c] = fmaf(-tz2, vu[c] * pzv_n[c], rv[c]);
+                        float z = tcx * fmaf(-W[c + 2], rx[c + 1], W[c] * rx[c]);
+                        z = fmaf(tcy, fmaf(-wn[c], V[c + 1] + vu[c], ws[c] * (vs[c] + vus[c])), z);
+                        z = fmaf(td1, wd[c] * pzw[c], z);
+                        rw[c] = fmaf(-td2, wu[c] * pzw_n[c], z);
+                    }
+                }
+            }
+
+            if (kk >= kb && valid) {
+                float a[4], b[4], d[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (MODE == MODE_STEP) {   // at kk = 1 the source terms are 0
+                        a[c] = fmaf(dt, ru[c], u0[c]);
+                        b[c] = fmaf(dt, rv[c], v0[c]);
+                        d[c] = fmaf(dt, rw[c], w0[c]);
+                    } else {
+                        a[c] = ru[c];
+                        b[c] = rv[c];
+                        d[c] = rw[c];
+                    }
+                    if (SCALED) {
+                        a[c] *= sc.out[0];
+                        b[c] *= sc.out[1];
+                        d[c] *= sc.out[2];
+                    }
+                }
+                Epilogue<T, MODE>::store4v(o0, o1, o2, row_off + (long long)kk * g.pk, a, b, d, g, j, i0);
+            }
+
+            // roll: level kk becomes level k-1, level kk+1 becomes level kk
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ud[c] = u0[c];
+                vd[c] = v0[c];
+                wd[c] = w0[c];
+                pzu[c] = pzu_n[c];
+                pzv[c] = pzv_n[c];
+                pzw[c] = pzw_n[c];
+                u0[c] = uu[c];
+                v0[c] = vu[c];
+                vs[c] = vus[c];
+                w0[c] = wu[c];
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) return false;
+        if (tid == 0 && issued < np) {
+            fence_proxy_async_smem();
+            issue(issued);   // plane lp + S into the slot level kk just released
+            ++issued;
+        }
+        return true;
+    };
+
+    // Blocks of S levels with the ring slots known at compile time (plane pb+lp
+    // sits in slot lp % S), then the remaining levels.
+    int kk = pb;
+    for (int blk = 0; PW_TMA_UNROLL && kk + S - 1 <= ke && !aborted; kk += S, ++blk) {
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+            if (!aborted && !level(kk + q, q, (q + 1) % S, (uint32_t)((blk + (q + 1) / S) & 1))) aborted = true;
+    }
+    for (; kk <= ke && !aborted; ++kk) {
+        const int lp = kk - pb;
+        if (!level(kk, lp % S, (lp + 1) % S, (uint32_t)(((lp + 1) / S) & 1))) aborted = true;
+    }
+
+    if (aborted && tid == 0) {
+        report_error(err, DEV_TIMEOUT_TMA_WAIT);
+        // let the copies still in flight land before the CTA's smem is released
+        for (int p = waited; p < issued; ++p)
+            if (!mbar_wait_bounded(&bars[p % S], (p / S) & 1, kDrainLimitNs)) break;
+    }
+}
+
+// Instantiated launch shapes: (ty, stages).
+#define PW_TMA_CONFIGS(X) X(4, 4) X(8, 3) X(8, 4) X(8, 6) X(16, 3) X(16, 4)
+
+template <typename T, int TY, int S, bool SC, int MODE>
+static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1,
+                                   void* o2, const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
+                                   cudaStream_t s) {
+    using L = TmaLayout<T, TY, S>;
+    auto kern = tma_kernel<T, TY, S, SC, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
+    dim3 block(32, TY);
+    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, sc, cf, dt,
+                                      err);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
+                                   const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
+                                   const TmaConfig& c, cudaStream_t s) {
+#define PW_DISPATCH(TY_, S_)                                                                                   \
+    if (c.ty == TY_ && c.stages == S_)                                                                         \
+        return scaled                                                                                          \
+                   ? launch_tma_inst<T, TY_, S_, true, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s) \
+                   : launch_tma_inst<T, TY_, S_, false, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s);
+    PW_TMA_CONFIGS(PW_DISPATCH)
+#undef PW_DISPATCH
+    return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace pw

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
+    ("pw_step", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _FP, _VP]),
     ("pw_error_norms", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32,
@@ -244,6 +245,17 @@ class PW:
         _check(lib().pw_tendencies_host(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"),
                                         _ptr(su, g, "su"), _ptr(sv, g, "sv"), _ptr(sw, g, "sw"),
                                         sp[0] if sp else None, _stream_ptr(stream)), "pw_tendencies_host")
+
+    def step(self, u, v, w, tmp_u, tmp_v, tmp_w, dt, nsteps, scale=None, stream=None):
+        """nsteps forward-Euler steps in place on (u, v, w); tmp_* are scratch."""
+        g = self.grid
+        sp = None
+        if scale is not None:
+            arr = (ctypes.c_float * 3)(*[float(x) for x in scale])
+            sp = (ctypes.cast(arr, _FP), arr)
+        _check(lib().pw_step(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"), _ptr(tmp_u, g, "tmp_u"),
+                             _ptr(tmp_v, g, "tmp_v"), _ptr(tmp_w, g, "tmp_w"), float(dt), int(nsteps),
+                             sp[0] if sp else None, _stream_ptr(stream)), "pw_step")
 
     def fill_halo_periodic(self, f, stream=None):
         _check(lib().pw_fill_halo_periodic(self.h, _ptr(f, self.grid, "f"), _stream_ptr(stream)),
