@@ -168,6 +168,38 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
 pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void *tmp_v, void *tmp_w,
                     float dt, int32_t nsteps, const float *scale, pw_stream_t stream);
 
+/* Flags of pw_adjoint. */
+#define PW_ADJ_ACCUMULATE 1  /* g += alpha * J^T l                        */
+#define PW_ADJ_PERIODIC   2  /* doubly periodic domain (see pw_adjoint)    */
+#define PW_ADJ_ADD_LAMBDA 4  /* g = l + alpha * J^T l (one reverse Euler step) */
+
+/*
+ * Adjoint of the PW scheme (Sec. 2.2) linearised about (u, v, w): given the
+ * sensitivities l = (lsu, lsv, lsw) of a scalar with respect to su, sv, sw,
+ * computes J(u,v,w)^T l, the sensitivities with respect to u, v, w, in gather
+ * form (no atomics), and writes
+ *     g = alpha * J^T l               (flags without ACCUMULATE/ADD_LAMBDA)
+ *     g = g + alpha * J^T l           (PW_ADJ_ACCUMULATE)
+ *     g = l + alpha * J^T l           (PW_ADJ_ADD_LAMBDA: the reverse sweep of
+ *                                      one forward-Euler step q + dt*s(q) with
+ *                                      alpha = dt, l = g_{n+1}, g = g_n)
+ * for g = (gu, gv, gw).  Only the entries of l at the scheme's outputs count
+ * (su, sv at levels 2..nz, sw at 2..nz-1, interior columns); the rest of l
+ * is ignored.
+ * Without PW_ADJ_PERIODIC the halo values of u, v, w are independent
+ * inputs: g is written on levels 1..nz of the interior and the one-cell
+ * lateral halo.  With PW_ADJ_PERIODIC the domain is doubly periodic: the
+ * halos of u, v, w must hold the periodic images (pw_fill_halo_periodic),
+ * output cells wrap around, and g is the sensitivity with respect to the
+ * interior values (the halo contributions folded onto their images); g is
+ * written on the interior only.  Cells of g not listed are not written.
+ * FP32 storage only (PW_ERR_UNSUPPORTED otherwise).  g must not alias any
+ * input.  A term whose sensitivity is exactly 0 is skipped.
+ */
+pw_status_t pw_adjoint(pw_handle_t h, const void *u, const void *v, const void *w,
+                       const void *lsu, const void *lsv, const void *lsw,
+                       void *gu, void *gv, void *gw, float alpha, int32_t flags, pw_stream_t stream);
+
 /*
  * Periodic lateral boundary: copy interior values into the lateral halo of
  * f (all halo columns and rows, corners included, levels k = 1..nz), as the

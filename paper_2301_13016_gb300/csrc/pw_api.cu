@@ -478,6 +478,32 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     return PW_OK;
 }
 
+pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* w, const void* lsu,
+                       const void* lsv, const void* lsw, void* gu, void* gv, void* gw, float alpha, int32_t flags,
+                       pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (h->grid.dtype != PW_F32) return fail(PW_ERR_UNSUPPORTED, "pw_adjoint supports FP32 fields only");
+    if (!u || !v || !w || !lsu || !lsv || !lsw || !gu || !gv || !gw) return fail(PW_ERR_ARG, "a field pointer is NULL");
+    if (flags & ~(PW_ADJ_ACCUMULATE | PW_ADJ_PERIODIC | PW_ADJ_ADD_LAMBDA)) return fail(PW_ERR_ARG, "unknown flag bits");
+    if ((flags & PW_ADJ_ACCUMULATE) && (flags & PW_ADJ_ADD_LAMBDA))
+        return fail(PW_ERR_ARG, "PW_ADJ_ACCUMULATE and PW_ADJ_ADD_LAMBDA are exclusive");
+    const void* ins[6] = {u, v, w, lsu, lsv, lsw};
+    const void* outs[3] = {gu, gv, gw};
+    for (auto o : outs)
+        for (auto i : ins)
+            if (o == i) return fail(PW_ERR_ARG, "an output aliases an input");
+    if (gu == gv || gu == gw || gv == gw) return fail(PW_ERR_ARG, "outputs alias each other");
+    if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return fail(PW_ERR_ARG, "alpha must be finite");
+    CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    cudaError_t e = launch_adjoint(to_dev(h->grid), (const float*)u, (const float*)v, (const float*)w,
+                                   (const float*)lsu, (const float*)lsv, (const float*)lsw, (float*)gu, (float*)gv,
+                                   (float*)gw, alpha, (flags & PW_ADJ_ACCUMULATE) ? 1 : 0,
+                                   (flags & PW_ADJ_ADD_LAMBDA) ? 1 : 0, (flags & PW_ADJ_PERIODIC) ? 1 : 0, cf,
+                                   h->num_sms, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+    return PW_OK;
+}
+
 pw_status_t pw_fill_halo_periodic(pw_handle_t h, void* f, pw_stream_t stream) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!f) return fail(PW_ERR_ARG, "field pointer is NULL");

@@ -63,6 +63,12 @@ cudaError_t launch_step_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUten
                             void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
                             const TmaConfig& c, cudaStream_t s);
 
+// Adjoint gather kernel (FP32 fields): g = [g | l | 0] + alpha * J(u,v,w)^T l.
+cudaError_t launch_adjoint(const GridDev& g, const float* u, const float* v, const float* w, const float* lu,
+                           const float* lv, const float* lw, float* gu, float* gv, float* gw, float alpha,
+                           int accumulate, int add_lambda, int periodic, const CoefDev& cf, int num_sms,
+                           cudaStream_t s);
+
 // Blocks of the TMA kernel resident per SM for a config (0 if it cannot launch).
 int tma_blocks_per_sm(pw_dtype_t dt, const TmaConfig& c);
 

@@ -17,6 +17,7 @@ import torch
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG_DIR, "libpw.so")
 
+PW_ADJ_ACCUMULATE, PW_ADJ_PERIODIC, PW_ADJ_ADD_LAMBDA = 1, 2, 4
 PW_OK, PW_ERR_ARG, PW_ERR_ALIGN, PW_ERR_CUDA, PW_ERR_OOM, PW_ERR_DEVICE_TIMEOUT, PW_ERR_UNSUPPORTED = range(7)
 DTYPES = {"f32": (0, torch.float32), "bf16": (1, torch.bfloat16), "f16": (2, torch.float16)}
 
@@ -55,6 +56,7 @@ SIGNATURES = [
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
+    ("pw_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _VP]),
     ("pw_step", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _FP, _VP]),
     ("pw_error_norms", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32, _dp, _VP]),
@@ -256,6 +258,13 @@ class PW:
         _check(lib().pw_step(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"), _ptr(tmp_u, g, "tmp_u"),
                              _ptr(tmp_v, g, "tmp_v"), _ptr(tmp_w, g, "tmp_w"), float(dt), int(nsteps),
                              sp[0] if sp else None, _stream_ptr(stream)), "pw_step")
+
+    def adjoint(self, u, v, w, lsu, lsv, lsw, gu, gv, gw, alpha=1.0, flags=0, stream=None):
+        """g = [g | l | 0] + alpha * J(u,v,w)^T l (see pw_adjoint for flags)."""
+        g = self.grid
+        _check(lib().pw_adjoint(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"), _ptr(lsu, g, "lsu"),
+                                _ptr(lsv, g, "lsv"), _ptr(lsw, g, "lsw"), _ptr(gu, g, "gu"), _ptr(gv, g, "gv"),
+                                _ptr(gw, g, "gw"), float(alpha), int(flags), _stream_ptr(stream)), "pw_adjoint")
 
     def fill_halo_periodic(self, f, stream=None):
         _check(lib().pw_fill_halo_periodic(self.h, _ptr(f, self.grid, "f"), _stream_ptr(stream)),
