@@ -119,11 +119,14 @@ pw_status_t pw_destroy(pw_handle_t h);
 pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
 
 /*
- * Launch shape of the TMA k-march kernel: ty = rows per CTA (4, 8 or 16),
- * stages = planes buffered per CTA (3..6), nseg = CTAs along z (0 = chosen
- * from the grid and SM count).  Any argument 0 keeps the automatic choice.
+ * Launch shape of the TMA k-march kernel: lanes_x = lanes per row (32: tiles
+ * 128 columns wide; 16: 64 columns, for narrow grids), ty = rows per CTA,
+ * stages = planes buffered per CTA, nseg = CTAs along z (0 = chosen from the
+ * grid and SM count).  Any argument 0 keeps the automatic choice (32, 4, 4).
+ * Instantiated shapes (lanes_x, ty, stages): (32,4,4) (32,8,3) (32,8,4)
+ * (32,8,6) (32,16,3) (16,4,4) (16,8,4); others give PW_ERR_UNSUPPORTED.
  */
-pw_status_t pw_set_tma_config(pw_handle_t h, int32_t ty, int32_t stages, int32_t nseg);
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t ty, int32_t stages, int32_t nseg);
 
 /*
  * Source terms su, sv, sw of the PW scheme (Sec. 2.2; arithmetic shape
@@ -254,6 +257,55 @@ pw_status_t pw_weighted_dot(pw_handle_t h, const void *a, float sa, const void *
 pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void *a, float sa, const void *b, float sb,
                                     const double *wk, int32_t k0, int32_t k1, double *out,
                                     pw_stream_t stream);
+
+/*
+ * Batched source terms: n independent grids, each with its own layout and
+ * coefficients (one dtype for all), in one persistent launch replayed from a
+ * CUDA graph.  The paper scales its design by decomposing the problem into
+ * independent compute units that each own part of the grid (Sec. 5); here a
+ * unit is a whole grid and every (grid, tile) pair is a work item, taken
+ * longest first from an atomic counter by one k-march CTA per SM slot.
+ * Every grid's layout must qualify for the k-march kernel (pw_grid_default
+ * layouts with nx a multiple of 4 do), else PW_ERR_UNSUPPORTED.
+ */
+typedef struct pw_batch_s *pw_batch_t;
+
+/* Create a batch: grids[n] and coeffs[n] (HOST arrays, copied).  Allocates
+ * the device tables and the work list; the tile shape starts at (32, 4, 4). */
+pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t *coeffs,
+                            pw_batch_t *out);
+
+/* Tile shape of the batched kernel: lanes_x (32 or 16), ty, stages from the
+ * instantiated set (32,4,4) (32,8,4) (16,4,4) (16,8,4); ctas_per_sm = resident
+ * CTAs per SM of the persistent launch (0 = as many as fit).  Rebuilds the
+ * work list; the next call captures a new graph.  The autotuner
+ * (paper_2301_13016_gb300.autotune) chooses these by measurement. */
+pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages,
+                                int32_t ctas_per_sm);
+
+/* Work items, interior cells and persistent CTAs of the current shape (any
+ * output pointer may be NULL). */
+pw_status_t pw_batch_info(pw_batch_t b, int64_t *n_items, int64_t *cells, int32_t *ctas);
+
+/*
+ * Source terms of every grid of the batch (as pw_tendencies per grid):
+ * u, v, w, su, sv, sw are HOST arrays of n DEVICE pointers, 16-byte aligned,
+ * in each grid's layout; scale as in pw_tendencies, shared by all grids.
+ * The first call, and any call whose pointers differ from the previous
+ * call's, synchronises `stream` and uploads the per-grid tables; the first
+ * call after pw_batch_create / pw_batch_set_config or a change of scale
+ * captures the graph (counter reset + persistent kernel).  Every call then
+ * launches the graph on `stream`.
+ */
+pw_status_t pw_batch_tendencies(pw_batch_t b, const void *const *u, const void *const *v,
+                                const void *const *w, void *const *su, void *const *sv,
+                                void *const *sw, const float *scale, pw_stream_t stream);
+
+/* pw_sync for a batch: wait for `stream`, report a recorded timeout. */
+pw_status_t pw_batch_sync(pw_batch_t b, pw_stream_t stream);
+
+/* Release the batch.  NULL is accepted. */
+pw_status_t pw_batch_destroy(pw_batch_t b);
 
 /* Wait for `stream`, then report (and clear) any bounded-wait timeout a
  * kernel of this handle recorded, and any pending CUDA error. */

@@ -1,0 +1,131 @@
+"""Autotuner for the k-march launch shapes.
+
+Measures each candidate shape on the caller's own buffers with CUDA events
+and keeps the fastest, caching the choice in a JSON file keyed by the grid
+shapes, the dtype, the GPU name and its SM count (the cache file is
+~/.cache/pw_gb300_tune.json unless a path is given).
+
+  tune_batch(batch, fields)   shape of the persistent batched kernel
+                              (lanes per row, rows, stages, CTAs per SM)
+  tune_grid(handle, fields)   shape of the single-grid kernel
+                              (lanes per row, rows, stages, k segments)
+"""
+import hashlib
+import json
+import os
+
+import torch
+
+BATCH_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=4, ctas_per_sm=c)
+                    for lx, ty in ((32, 4), (32, 8), (16, 4), (16, 8)) for c in (0, 2)]
+GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns)
+                   for lx, ty, st in ((32, 4, 4), (32, 8, 4), (32, 8, 6), (16, 4, 4), (16, 8, 4))
+                   for ns in (0, 1, 2, 4)]
+
+
+def _default_cache():
+    return os.path.join(os.path.expanduser("~"), ".cache", "pw_gb300_tune.json")
+
+
+def _device_key():
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}"
+
+
+def _signature(kind, shapes, dtype):
+    h = hashlib.sha256(json.dumps([kind, dtype, shapes]).encode()).hexdigest()[:20]
+    return f"{kind}|{dtype}|{_device_key()}|{h}"
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, key, value):
+    data = _load(path)
+    data[key] = value
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time(fn, warmup, reps, stream):
+    for _ in range(warmup):
+        fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(batch, fields, candidates=None, warmup=2, reps=5, cache_path=None, force=False):
+    """Pick and apply the fastest batched-kernel shape for `batch`.
+    fields = (us, vs, ws, sus, svs, sws), lists of flat device tensors.
+    Returns (config, {config string: ms})."""
+    cache_path = cache_path or _default_cache()
+    shapes = [[g.nx, g.ny, g.nz] for g in batch.grids]
+    key = _signature("batch", shapes, batch.grids[0].dtype)
+    cached = _load(cache_path).get(key)
+    if cached and not force:
+        batch.set_config(**cached["config"])
+        return cached["config"], cached.get("times", {})
+    stream = torch.cuda.current_stream()
+    times = {}
+    best, best_ms = None, float("inf")
+    for c in candidates or BATCH_CANDIDATES:
+        try:
+            batch.set_config(**c)
+        except RuntimeError:
+            continue
+        ms = _time(lambda: batch.tendencies(*fields, stream=stream), warmup, reps, stream)
+        batch.sync(stream)
+        times[json.dumps(c, sort_keys=True)] = ms
+        if ms < best_ms:
+            best, best_ms = c, ms
+    if best is None:
+        raise RuntimeError("no batched kernel shape could run")
+    batch.set_config(**best)
+    _store(cache_path, key, {"config": best, "times": times})
+    return best, times
+
+
+def tune_grid(handle, fields, candidates=None, warmup=2, reps=5, cache_path=None, force=False):
+    """Pick and apply the fastest single-grid k-march shape for `handle`.
+    fields = (u, v, w, su, sv, sw) flat device tensors.  Returns (config, times)."""
+    cache_path = cache_path or _default_cache()
+    g = handle.grid
+    key = _signature("grid", [[g.nx, g.ny, g.nz]], g.dtype)
+    cached = _load(cache_path).get(key)
+    if cached and not force:
+        handle.set_tma_config(**cached["config"])
+        return cached["config"], cached.get("times", {})
+    stream = torch.cuda.current_stream()
+    times = {}
+    best, best_ms = None, float("inf")
+    for c in candidates or GRID_CANDIDATES:
+        if c["nseg"] > g.nz // 2:
+            continue
+        try:
+            handle.set_tma_config(**c)
+        except RuntimeError:
+            continue
+        ms = _time(lambda: handle.tendencies(*fields, stream=stream), warmup, reps, stream)
+        handle.sync(stream)
+        times[json.dumps(c, sort_keys=True)] = ms
+        if ms < best_ms:
+            best, best_ms = c, ms
+    if best is None:
+        raise RuntimeError("no k-march shape could run")
+    handle.set_tma_config(**best)
+    _store(cache_path, key, {"config": best, "times": times})
+    return best, times

@@ -58,7 +58,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 struct MapCacheEntry {
     const void* ptr = nullptr;
-    int ty = 0;
+    int ty = 0, lx = 0;
     CUtensorMap map;
 };
 
@@ -75,8 +75,8 @@ struct pw_handle_s {
     int* d_err = nullptr;       // device status word (bounded-wait timeouts)
     int kernel_kind = 0;        // 0 auto, 1 generic, 2 TMA
     int last_kernel = 0;
-    TmaConfig tma_user{0, 0, 0};
-    TmaConfig tma_auto{0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
+    TmaConfig tma_user{0, 0, 0, 0};
+    TmaConfig tma_auto{0, 0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
     // pw_tendencies_host staging
@@ -104,7 +104,7 @@ static long long alloc_elems_of(const pw_grid_t& g) {
            1;
 }
 
-static pw_status_t validate_grid(const pw_grid_t* g) {
+pw_status_t pw::validate_grid(const pw_grid_t* g) {
     if (!g) return fail(PW_ERR_ARG, "grid is NULL");
     if (g->dtype != PW_F32 && g->dtype != PW_BF16 && g->dtype != PW_F16)
         return fail(PW_ERR_ARG, "unknown dtype %d", (int)g->dtype);
@@ -124,7 +124,7 @@ static pw_status_t validate_grid(const pw_grid_t* g) {
 
 // TMA eligibility of the layout (pointer alignment is checked per call).
 // Writes the x offset `ox` of element i = 0 within its padded row.
-static bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
+bool pw::tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
     const long long es = (long long)dtype_size(g.dtype);
     const long long padx = 16 / es;
     if (g.nx % 4) { *why = "nx is not a multiple of 4"; return false; }
@@ -138,19 +138,28 @@ static bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
     return true;
 }
 
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool pw::aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int ty, CUtensorMap* out) {
+static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out) {
     for (auto& c : h->maps)
-        if (c.ptr == ptr && c.ty == ty) {
+        if (c.ptr == ptr && c.ty == ty && c.lx == lx) {
             *out = c.map;
             return PW_OK;
         }
     MapCacheEntry& e = h->maps[h->map_next];
     h->map_next = (h->map_next + 1) % (int)(sizeof(h->maps) / sizeof(h->maps[0]));
+    pw_status_t st = encode_tensor_map(h->grid, ptr, ox, lx, ty, out);
+    if (st != PW_OK) return st;
+    e.ptr = ptr;
+    e.ty = ty;
+    e.lx = lx;
+    e.map = *out;
+    return PW_OK;
+}
+
+pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out) {
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const pw_grid_t& g = h->grid;
     const size_t es = dtype_size(g.dtype);
     CUtensorMapDataType dt = g.dtype == PW_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : g.dtype == PW_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -158,15 +167,12 @@ static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int ty, CU
     cuuint64_t dims[3] = {(cuuint64_t)(ox + g.nx + g.halo + 1), (cuuint64_t)(g.ny + 2 * g.halo),
                           (cuuint64_t)(g.nz + 2)};
     cuuint64_t strides[2] = {(cuuint64_t)(g.pitch_j * es), (cuuint64_t)(g.pitch_k * es)};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype, lx), (cuuint32_t)(ty + 2), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(out, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
-    e.ptr = ptr;
-    e.ty = ty;
-    e.map = *out;
     return PW_OK;
 }
 
@@ -176,12 +182,14 @@ static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int ty, CU
 static TmaConfig choose_tma(pw_handle_t h) {
     if (h->tma_auto.ty) return h->tma_auto;
     TmaConfig c;
+    c.lx = h->tma_user.lx ? h->tma_user.lx : 32;
     c.ty = h->tma_user.ty ? h->tma_user.ty : 4;
     c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
     if (h->tma_user.nseg) {
         c.nseg = h->tma_user.nseg;
     } else {
-        const long long tiles = (long long)((h->grid.nx + 127) / 128) * ((h->grid.ny + c.ty - 1) / c.ty);
+        const long long tiles =
+            (long long)((h->grid.nx + 4 * c.lx - 1) / (4 * c.lx)) * ((h->grid.ny + c.ty - 1) / c.ty);
         int bps = tma_blocks_per_sm(h->grid.dtype, c);
         if (bps < 1) bps = 1;
         const long long slots = (long long)h->num_sms * bps;
@@ -303,14 +311,15 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind) {
     return PW_OK;
 }
 
-pw_status_t pw_set_tma_config(pw_handle_t h, int32_t ty, int32_t stages, int32_t nseg) {
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t ty, int32_t stages, int32_t nseg) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
-    TmaConfig c{ty ? ty : 4, stages ? stages : 4, 1};
+    TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
     if (!tma_config_supported(h->grid.dtype, c))
-        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for ty=%d stages=%d", c.ty, c.stages);
-    h->tma_user = TmaConfig{ty, stages, nseg};
-    h->tma_auto = TmaConfig{0, 0, 0};
+        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for lanes_x=%d ty=%d stages=%d", c.lx, c.ty,
+                    c.stages);
+    h->tma_user = TmaConfig{lanes_x, ty, stages, nseg};
+    h->tma_auto = TmaConfig{0, 0, 0, 0};
     for (auto& m : h->maps) m.ptr = nullptr;
     return PW_OK;
 }
@@ -352,7 +361,7 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         TmaConfig c = choose_tma(h);
         CUtensorMap maps[3];
         for (int q = 0; q < 3; ++q) {
-            pw_status_t st = encode_map(h, ins[q], ox, c.ty, &maps[q]);
+            pw_status_t st = encode_map(h, ins[q], ox, c.lx, c.ty, &maps[q]);
             if (st != PW_OK) return st;
         }
         cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, scaled, cf, h->d_err, c, s);
@@ -448,7 +457,7 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
         if (use_tma) {
             CUtensorMap maps[3];
             for (int q = 0; q < 3; ++q) {
-                pw_status_t st = encode_map(h, src[q], ox, c.ty, &maps[q]);
+                pw_status_t st = encode_map(h, src[q], ox, c.lx, c.ty, &maps[q]);
                 if (st != PW_OK) return st;
             }
             e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);

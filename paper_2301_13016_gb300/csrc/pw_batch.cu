@@ -1,0 +1,413 @@
+// Batched PW source terms: many independent grids of uneven sizes in one
+// persistent launch, replayed from a CUDA graph.
+//
+// The paper scales its Versal design by decomposing the problem into
+// independent compute units, each owning a 3D part of the grid (Sec. 5);
+// here the units are whole grids.  Every (grid, tile) pair is a work item;
+// the items are sorted longest first and a persistent k-march CTA per SM
+// slot takes the next item from an atomic counter until none is left, so
+// large and small grids share the GPU without a launch per grid.  The
+// per-grid records and TMA descriptors live in device tables that are
+// re-uploaded only when the field pointers change; the counter reset and the
+// kernel are captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pw_stencil.cuh"
+
+namespace pw {
+
+struct BatchGridDev {
+    GridDev g;
+    int ox, tiles_x, tiles_y, nseg;
+    float tcx, tcy;
+    const float* tz;
+    void* o[3];
+};
+
+template <typename T, int LX, int TY, int S, bool SCALED>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (tma_min_blocks<T, LX, TY, S>()))
+    tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
+                     const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
+                     int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MarchSmem<T, LX, TY, S> sm(smem_raw);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    sm.init(tid);
+    uint32_t ring = 0;
+    for (;;) {
+        if (tid == 0) sm.flag[1] = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = sm.flag[1];
+        __syncthreads();   // every thread has read the item before it is overwritten
+        if (it >= n_items) break;
+        const int2 item = items[it];
+        const BatchGridDev& bg = grids[item.x];
+        const int per_seg = bg.tiles_x * bg.tiles_y;
+        const int seg = item.y / per_seg;
+        const int rem = item.y - seg * per_seg;
+        const int by = rem / bg.tiles_x, bx = rem - by * bg.tiles_x;
+        const int nz = bg.g.nz;
+        const int kb = 1 + (int)(((long long)seg * nz) / bg.nseg);
+        const int ke = (int)(((long long)(seg + 1) * nz) / bg.nseg);
+        const CoefDev cf{bg.tcx, bg.tcy, bg.tz};
+        const CUtensorMap* m = maps + 3 * (size_t)item.x;
+        if (!march_tile<T, LX, TY, S, SCALED, MODE_TEND>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1],
+                                                         (T*)bg.o[2], bg.g, bg.ox, sc, cf, 0.f, bx, by, kb, ke,
+                                                         ring, err))
+            break;
+    }
+}
+
+#define PW_BATCH_CONFIGS(X) X(32, 4, 4) X(32, 8, 4) X(16, 4, 4) X(16, 8, 4)
+
+template <typename T, int LX, int TY, int S, bool SC>
+static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,
+                              const int2* items, int n_items, int* counter, const Scales& sc, int* err, int ctas,
+                              cudaStream_t s) {
+    using L = TmaLayout<T, LX, TY, S>;
+    auto kern = tma_batch_kernel<T, LX, TY, S, SC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    if (e != cudaSuccess) return e;
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
+    kern<<<ctas, dim3(32, L::WARPS), L::SMEM, s>>>(grids, maps, items, n_items, counter, sc, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t batch_t(const TmaConfig& c, bool scaled, bool query, int* bps, const BatchGridDev* grids,
+                           const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
+                           int* err, int ctas, cudaStream_t s) {
+#define PW_BD(LX_, TY_, S_)                                                                                      \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                            \
+        return scaled ? batch_inst<T, LX_, TY_, S_, true>(query, bps, grids, maps, items, n_items, counter, sc, err, \
+                                                          ctas, s)                                               \
+                      : batch_inst<T, LX_, TY_, S_, false>(query, bps, grids, maps, items, n_items, counter, sc,     \
+                                                           err, ctas, s);
+    PW_BATCH_CONFIGS(PW_BD)
+#undef PW_BD
+    return cudaErrorInvalidConfiguration;
+}
+
+static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool scaled, bool query, int* bps,
+                                  const BatchGridDev* grids, const CUtensorMap* maps, const int2* items, int n_items,
+                                  int* counter, const Scales& sc, int* err, int ctas, cudaStream_t s) {
+    switch (dt) {
+        case PW_F32: return batch_t<float>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+        case PW_BF16:
+            return batch_t<__nv_bfloat16>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+        case PW_F16: return batch_t<__half>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static bool batch_config_supported(const TmaConfig& c) {
+#define PW_BS(LX_, TY_, S_) \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_) return true;
+    PW_BATCH_CONFIGS(PW_BS)
+#undef PW_BS
+    return false;
+}
+
+}  // namespace pw
+
+using namespace pw;
+
+struct pw_batch_s {
+    int n = 0;
+    pw_dtype_t dtype = PW_F32;
+    int device = 0, num_sms = 0;
+    std::vector<pw_grid_t> grids;
+    std::vector<int> ox;
+    std::vector<float> tcx, tcy;
+    std::vector<size_t> tz_off;
+    float* d_tz = nullptr;
+    BatchGridDev* d_grids = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    int2* d_items = nullptr;
+    int* d_counter = nullptr;
+    int* d_err = nullptr;
+    BatchGridDev* h_grids = nullptr;   // pinned staging
+    CUtensorMap* h_maps = nullptr;
+    std::vector<int2> items;
+    long long cells = 0;
+    TmaConfig cfg{32, 4, 4, 1};
+    int ctas_per_sm = 0;    // 0 = occupancy
+    int ctas = 0;
+    std::vector<const void*> ptrs;   // 6n pointers the tables were built for
+    bool tables_ok = false, items_ok = false;
+    Scales graph_sc{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
+    bool graph_scaled = false;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static pw_status_t bfail(pw_status_t s, const char* msg) { return internal_fail(s, "%s", msg); }
+
+static void drop_graph(pw_batch_t b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Work items for the current tile shape, longest first (levels, then width).
+static pw_status_t build_items(pw_batch_t b) {
+    const int TX = 4 * b->cfg.lx, TY = b->cfg.ty;
+    struct Item {
+        int grid, tile;
+        long long cost;
+    };
+    std::vector<Item> v;
+    for (int q = 0; q < b->n; ++q) {
+        const pw_grid_t& g = b->grids[q];
+        const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
+        for (int t = 0; t < tx * ty; ++t) {
+            const int bx = t % tx;
+            const int width = std::min(TX, g.nx - bx * TX);
+            v.push_back({q, t, (long long)(g.nz + 1) * 1024 + width});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
+    b->items.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) b->items[i] = make_int2(v[i].grid, v[i].tile);
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(1, v.size()) * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_items, b->items.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return internal_cuda_fail(e, "batch work list upload");
+    int bps = 0;
+    Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
+    e = batch_dispatch(b->dtype, b->cfg, false, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
+                       nullptr);
+    if (e != cudaSuccess || bps < 1) return internal_cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                                                               "batch kernel occupancy");
+    const int per_sm = b->ctas_per_sm ? std::min(b->ctas_per_sm, bps) : bps;
+    b->ctas = b->num_sms * per_sm;
+    b->items_ok = true;
+    b->tables_ok = false;
+    drop_graph(b);
+    return PW_OK;
+}
+
+extern "C" {
+
+pw_status_t pw_batch_create(int32_t n, const pw_grid_t* grids, const pw_coeffs_t* coeffs, pw_batch_t* out) {
+    if (!out) return bfail(PW_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !grids || !coeffs) return bfail(PW_ERR_ARG, "need n >= 1 grids and coefficient sets");
+    pw_batch_s* b = new (std::nothrow) pw_batch_s();
+    if (!b) return bfail(PW_ERR_OOM, "host allocation of the batch failed");
+    b->n = n;
+    b->dtype = grids[0].dtype;
+    size_t tz_total = 0;
+    for (int q = 0; q < n; ++q) {
+        pw_status_t s = validate_grid(&grids[q]);
+        if (s != PW_OK) {
+            delete b;
+            return s;
+        }
+        if (grids[q].dtype != b->dtype) {
+            delete b;
+            return bfail(PW_ERR_ARG, "all grids of a batch must share one dtype");
+        }
+        int ox = 0;
+        const char* why = "";
+        if (!tma_layout_ok(grids[q], &ox, &why)) {
+            delete b;
+            return internal_fail(PW_ERR_UNSUPPORTED, "batch grid %d: layout not eligible for the k-march kernel (%s)",
+                                 q, why);
+        }
+        const pw_coeffs_t& c = coeffs[q];
+        if (!c.tzc1 || !c.tzc2 || !c.tzd1 || !c.tzd2) {
+            delete b;
+            return bfail(PW_ERR_ARG, "a vertical coefficient array is NULL");
+        }
+        b->grids.push_back(grids[q]);
+        b->ox.push_back(ox);
+        b->tcx.push_back((float)c.tcx);
+        b->tcy.push_back((float)c.tcy);
+        b->tz_off.push_back(tz_total);
+        tz_total += 4 * (size_t)(grids[q].nz + 2);
+        b->cells += (long long)grids[q].nx * grids[q].ny * grids[q].nz;
+    }
+    std::vector<float> tz(tz_total);
+    for (int q = 0; q < n; ++q) {
+        const int m = grids[q].nz + 2;
+        float* t = tz.data() + b->tz_off[q];
+        for (int k = 0; k < m; ++k) {
+            t[k] = (float)coeffs[q].tzc1[k];
+            t[m + k] = (float)coeffs[q].tzc2[k];
+            t[2 * m + k] = (float)coeffs[q].tzd1[k];
+            t[3 * m + k] = (float)coeffs[q].tzd2[k];
+        }
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tz, tz.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, n * sizeof(BatchGridDev));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, 3 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_grids, n * sizeof(BatchGridDev));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_maps, 3 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pw_batch_destroy(b);
+        return internal_cuda_fail(e, "pw_batch_create");
+    }
+    pw_status_t s = build_items(b);
+    if (s != PW_OK) {
+        pw_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return PW_OK;
+}
+
+pw_status_t pw_batch_destroy(pw_batch_t b) {
+    if (!b) return PW_OK;
+    drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_tz);
+    cudaFree(b->d_grids);
+    cudaFree(b->d_maps);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_err);
+    cudaFreeHost(b->h_grids);
+    cudaFreeHost(b->h_maps);
+    delete b;
+    return PW_OK;
+}
+
+pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages, int32_t ctas_per_sm) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
+    if (!batch_config_supported(c))
+        return internal_fail(PW_ERR_UNSUPPORTED, "no batched kernel instance for lanes_x=%d ty=%d stages=%d", c.lx,
+                             c.ty, c.stages);
+    if (ctas_per_sm < 0) return bfail(PW_ERR_ARG, "ctas_per_sm must be >= 0");
+    b->cfg = c;
+    b->ctas_per_sm = ctas_per_sm;
+    return build_items(b);
+}
+
+pw_status_t pw_batch_info(pw_batch_t b, int64_t* n_items, int64_t* cells, int32_t* ctas) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (n_items) *n_items = (int64_t)b->items.size();
+    if (cells) *cells = b->cells;
+    if (ctas) *ctas = b->ctas;
+    return PW_OK;
+}
+
+pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* const* v, const void* const* w,
+                                void* const* su, void* const* sv, void* const* sw, const float* scale,
+                                pw_stream_t stream) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (!u || !v || !w || !su || !sv || !sw) return bfail(PW_ERR_ARG, "a pointer table is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scales sc;
+    bool scaled = false;
+    for (int q = 0; q < 3; ++q) {
+        sc.in[q] = scale ? scale[q] : 1.f;
+        sc.out[q] = scale ? scale[3 + q] : 1.f;
+        if (!(sc.in[q] > 0.f) || !(sc.out[q] > 0.f) || !(sc.in[q] < 3.0e38f) || !(sc.out[q] < 3.0e38f))
+            return bfail(PW_ERR_ARG, "scales must be finite and > 0");
+        if (sc.in[q] != 1.f || sc.out[q] != 1.f) scaled = true;
+    }
+    // pointer tables: validate, and rebuild the device tables if they changed
+    std::vector<const void*> p(6 * (size_t)b->n);
+    for (int q = 0; q < b->n; ++q) {
+        const void* f[6] = {u[q], v[q], w[q], su[q], sv[q], sw[q]};
+        for (int a = 0; a < 6; ++a) {
+            if (!f[a]) return bfail(PW_ERR_ARG, "a field pointer is NULL");
+            if (!aligned16(f[a])) return bfail(PW_ERR_ALIGN, "batched fields must be 16-byte aligned");
+            for (int c = 3; c < 6; ++c)
+                if (a < 3 && f[a] == f[c]) return bfail(PW_ERR_ARG, "an output aliases an input");
+            p[6 * (size_t)q + a] = f[a];
+        }
+    }
+    if (!b->tables_ok || p != b->ptrs) {
+        // the pinned staging may still feed an earlier upload on this stream
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return internal_cuda_fail(e, "batch stream synchronize");
+        for (int q = 0; q < b->n; ++q) {
+            const pw_grid_t& g = b->grids[q];
+            for (int a = 0; a < 3; ++a) {
+                pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->ox[q], b->cfg.lx, b->cfg.ty,
+                                                   &b->h_maps[3 * (size_t)q + a]);
+                if (st != PW_OK) return st;
+            }
+            BatchGridDev& r = b->h_grids[q];
+            r.g.nx = g.nx;
+            r.g.ny = g.ny;
+            r.g.nz = g.nz;
+            r.g.halo = g.halo;
+            r.g.pj = g.pitch_j;
+            r.g.pk = g.pitch_k;
+            r.g.origin = g.origin;
+            r.ox = b->ox[q];
+            r.tiles_x = (g.nx + 4 * b->cfg.lx - 1) / (4 * b->cfg.lx);
+            r.tiles_y = (g.ny + b->cfg.ty - 1) / b->cfg.ty;
+            r.nseg = 1;
+            r.tcx = b->tcx[q];
+            r.tcy = b->tcy[q];
+            r.tz = b->d_tz + b->tz_off[q];
+            for (int a = 0; a < 3; ++a) r.o[a] = const_cast<void*>(p[6 * (size_t)q + 3 + a]);
+        }
+        e = cudaMemcpyAsync(b->d_grids, b->h_grids, b->n * sizeof(BatchGridDev), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_maps, b->h_maps, 3 * (size_t)b->n * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                                s);
+        if (e != cudaSuccess) return internal_cuda_fail(e, "batch table upload");
+        b->ptrs = p;
+        b->tables_ok = true;
+    }
+    // the graph: counter reset + persistent kernel, captured once per config
+    if (b->exec && (scaled != b->graph_scaled || (scaled && std::memcmp(&sc, &b->graph_sc, sizeof sc) != 0)))
+        drop_graph(b);
+    if (!b->exec) {
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
+        if (e == cudaSuccess)
+            e = batch_dispatch(b->dtype, b->cfg, scaled, false, nullptr, b->d_grids, b->d_maps, b->d_items,
+                               (int)b->items.size(), b->d_counter, sc, b->d_err, b->ctas, b->cap);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, gr, 0);
+        if (e != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            b->exec = nullptr;
+            return internal_cuda_fail(e, "batch graph capture");
+        }
+        b->graph = gr;
+        b->graph_sc = sc;
+        b->graph_scaled = scaled;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    if (e != cudaSuccess) return internal_cuda_fail(e, "batch graph launch");
+    return PW_OK;
+}
+
+pw_status_t pw_batch_sync(pw_batch_t b, pw_stream_t stream) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return internal_cuda_fail(e, "stream synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return internal_cuda_fail(e, "status word read");
+    if (flag != DEV_OK) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return internal_fail(PW_ERR_DEVICE_TIMEOUT, "a batched kernel gave up a bounded wait (code %d)", flag);
+    }
+    return PW_OK;
+}
+
+}  // extern "C"

@@ -32,7 +32,8 @@ struct CoefDev {
 
 // Launch shape of the TMA k-march kernel.
 struct TmaConfig {
-    int ty;      // interior rows per CTA (one warp per row, 128 columns)
+    int lx;      // lanes per row: 32 (tile 128 columns wide) or 16 (64 columns)
+    int ty;      // interior rows per CTA
     int stages;  // planes resident or in flight per CTA
     int nseg;    // k segments (CTAs along z)
 };
@@ -43,9 +44,8 @@ cudaError_t launch_tend_generic(pw_dtype_t dt, const GridDev& g, const void* u, 
                                 void* su, void* sv, void* sw, const Scales& sc, bool scaled,
                                 const CoefDev& cf, int num_sms, cudaStream_t s);
 
-// Box width (elements along x) of one TMA load for this dtype and the row
-// count of a box for a given ty.
-int tma_box_width(pw_dtype_t dt);
+// Box width (elements along x) of one TMA load for this dtype and tile width.
+int tma_box_width(pw_dtype_t dt, int lx);
 // True if an instantiation exists for (dtype, ty, stages).
 bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c);
 size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c);
@@ -90,5 +90,11 @@ cudaError_t launch_weighted_dot(pw_dtype_t dt, const GridDev& g, const void* a, 
 pw_status_t internal_fail(pw_status_t s, const char* fmt, ...);
 pw_status_t internal_cuda_fail(cudaError_t e, const char* what);
 bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
+
+// Layout checks and TMA descriptors shared by the single-grid and batched paths.
+pw_status_t validate_grid(const pw_grid_t* g);
+bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why);
+bool aligned16(const void* p);
+pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out);
 
 }  // namespace pw

@@ -174,30 +174,39 @@ static cudaError_t launch_generic_mode(const GridDev& g, const void* u, const vo
     return cudaGetLastError();
 }
 
+
 // ---------------------------------------------------------------------------
-// TMA k-march kernel.
+// TMA k-march.
 //
-// A CTA owns an x-y tile of 128 x TY interior columns and one k segment, and
+// A tile is TX = 4*LX interior columns by TY rows and one k segment; the CTA
 // marches up the column one level at a time.  Level planes of u, v, w (the
 // tile plus a one-cell halo, widened in x to the 16-byte TMA granule) arrive
-// in a ring of S shared-memory stages by 3D TMA box copies that one thread
-// issues, each stage completing on its own mbarrier; S-1 planes are in flight
+// in a ring of S shared-memory slots by 3D TMA box copies that one thread
+// issues, each slot completing on its own mbarrier; S-1 planes are in flight
 // ahead of the level being computed, so every input element is read from HBM
 // once and the copy engine, not the warps, keeps bytes in flight.
 //
-// Thread (lane, ty) computes 4 consecutive cells along x of row ty.  Shared
-// memory rows are read as 16-byte (FP32) or 8-byte (16-bit) vectors; x
-// neighbours come from the adjacent lanes by warp shuffles (the two
-// tile-edge lanes read theirs from the halo columns); y neighbours from the
+// LX lanes cover one row (LX = 32: one warp per row; LX = 16: two rows per
+// warp, for narrow grids).  A thread computes 4 consecutive cells along x.
+// Shared-memory rows are read as 16-byte (FP32) or 8-byte (16-bit) vectors; x
+// neighbours come from the adjacent lanes by warp shuffles (the two tile-edge
+// lanes of a row read theirs from the halo columns); y neighbours from the
 // rows above and below.  Registers carry from one level to the next: the
 // level-k+1 rows the upper terms read (they are the level-k rows of the next
-// step), the level k-1 values at the cell (a rolling window in z), and the
+// step), the level-(k-1) values at the cell (a rolling window in z), and the
 // three vertical pair sums of the upper fluxes, which are the lower pair sums
 // of the next level.  Pair sums along x are shared by neighbouring cells of a
 // thread.  Outputs go straight from registers to HBM as full vectors.
-template <typename T, int TY, int S>
+//
+// Ring bookkeeping is global to the CTA: the n-th plane a CTA ever issues
+// goes to slot n % S and completes phase (n / S) & 1 of that slot's mbarrier,
+// so a persistent CTA can march tile after tile without re-initialising.
+template <typename T, int LX, int TY, int S>
 struct TmaLayout {
-    static constexpr int TX = 128;
+    static constexpr int TX = 4 * LX;
+    static constexpr int RPW = 32 / LX;                // rows per warp
+    static constexpr int WARPS = TY / RPW;
+    static constexpr int THREADS = 32 * WARPS;
     static constexpr int PADX = 16 / (int)sizeof(T);   // elements in one 16-byte granule
     static constexpr int BW = TX + 2 * PADX;           // box width
     static constexpr int ROWS = TY + 2;
@@ -207,6 +216,8 @@ struct TmaLayout {
     static constexpr int STAGE = 3 * FIELD;
     static constexpr uint32_t TX_BYTES = 3u * FIELD_RAW * (uint32_t)sizeof(T);
     static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16;
+    static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
+    static_assert(TY % RPW == 0, "TY must be a multiple of the rows per warp");
 };
 
 // Build-time knobs of the k-march kernel (defaults are the measured best):
@@ -223,74 +234,99 @@ struct TmaLayout {
 
 // Resident CTAs per SM the register budget is sized for: what shared memory
 // and the thread limit allow, at most PW_TMA_MAX_MINB.
-template <typename T, int TY, int S>
+template <typename T, int LX, int TY, int S>
 constexpr int tma_min_blocks() {
-    constexpr int by_smem = (int)((227u * 1024u) / TmaLayout<T, TY, S>::SMEM);
-    constexpr int by_threads = 2048 / (32 * TY);
+    using L = TmaLayout<T, LX, TY, S>;
+    constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
+    constexpr int by_threads = 2048 / L::THREADS;
     constexpr int m = by_smem < by_threads ? by_smem : by_threads;
     return m < 1 ? 1 : (m > PW_TMA_MAX_MINB ? PW_TMA_MAX_MINB : m);
 }
 
-template <typename T, int TY, int S, bool SCALED, int MODE>
-__global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
-    tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
-               const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
-               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const Scales sc,
-               const CoefDev cf, const float dt, int* __restrict__ err) {
-    using L = TmaLayout<T, TY, S>;
+// Shared memory of a k-march CTA: the plane ring, one mbarrier per slot, and
+// the abort flag / work-item word.
+template <typename T, int LX, int TY, int S>
+struct MarchSmem {
+    using L = TmaLayout<T, LX, TY, S>;
+    T* stages;
+    uint64_t* bars;
+    volatile int* flag;   // flag[0]: abort, flag[1]: work item broadcast
+    __device__ __forceinline__ MarchSmem(unsigned char* raw) {
+        stages = reinterpret_cast<T*>(raw);
+        bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * L::STAGE * sizeof(T));
+        flag = reinterpret_cast<volatile int*>(bars + S);
+    }
+    // one thread, then a CTA barrier
+    __device__ __forceinline__ void init(int tid) {
+        if (tid == 0) {
+            for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+            flag[0] = 0;
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+};
+
+// March one tile: columns bx, rows by, output levels kb..ke of grid g.
+// `ring` counts the planes this CTA issued before; it is advanced by the
+// planes of this tile.  Returns false if a wait timed out (the error is
+// recorded and the copies in flight are drained).
+template <typename T, int LX, int TY, int S, bool SCALED, int MODE>
+__device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, const CUtensorMap* tm_u,
+                                           const CUtensorMap* tm_v, const CUtensorMap* tm_w, T* __restrict__ o0,
+                                           T* __restrict__ o1, T* __restrict__ o2, const GridDev& g, const int ox,
+                                           const Scales& sc, const CoefDev& cf, const float dt, const int bx,
+                                           const int by, const int kb, const int ke, uint32_t& ring,
+                                           int* __restrict__ err) {
+    using L = TmaLayout<T, LX, TY, S>;
     constexpr int BW = L::BW;
     constexpr int PADX = L::PADX;
     constexpr int FU = 0, FV = L::FIELD, FW = 2 * L::FIELD;
+    T* const stages = sm.stages;
+    uint64_t* const bars = sm.bars;
+    volatile int* const abort_flag = sm.flag;
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* stages = reinterpret_cast<T*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * L::STAGE * sizeof(T));
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S);
-
-    const int lane = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * 32 + lane;
-    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int tid = warp * 32 + lane;
+    const int xl = lane % LX;                          // lane within the row
+    const int row = warp * L::RPW + lane / LX;         // 0 .. TY-1
     const int nz = g.nz;
-    const int kb = 1 + (int)(((long long)bz * nz) / nseg);
-    const int ke = (int)(((long long)(bz + 1) * nz) / nseg);
     const int pb = max(kb - 1, 1);
     const int pe = min(ke + 1, nz);
     const int np = pe - pb + 1;
-    if (ke < kb) return;   // empty k segment (the host never launches one)
+    const uint32_t base = ring;
+    ring += (uint32_t)np;
 
     const int X0 = ox + 1 + L::TX * bx - PADX;
     const int Y0 = TY * by + g.halo - 1;
 
-    auto issue = [&](int p) {   // plane pb+p into stage p % S
-        const int s = p % S;
+    auto issue = [&](int p) {   // plane pb+p into slot (base+p) % S
+        const uint32_t n = base + (uint32_t)p;
+        const int s = (int)(n % S);
         T* dst = stages + s * L::STAGE;
         mbar_arrive_expect_tx(&bars[s], L::TX_BYTES);
-        tma_load_3d(dst + FU, &tm_u, X0, Y0, pb + p, &bars[s]);
-        tma_load_3d(dst + FV, &tm_v, X0, Y0, pb + p, &bars[s]);
-        tma_load_3d(dst + FW, &tm_w, X0, Y0, pb + p, &bars[s]);
+        tma_load_3d(dst + FU, tm_u, X0, Y0, pb + p, &bars[s]);
+        tma_load_3d(dst + FV, tm_v, X0, Y0, pb + p, &bars[s]);
+        tma_load_3d(dst + FW, tm_w, X0, Y0, pb + p, &bars[s]);
     };
+    auto slot = [&](int p) { return (int)((base + (uint32_t)p) % S); };
+    auto parity = [&](int p) { return (uint32_t)(((base + (uint32_t)p) / S) & 1u); };
 
     int issued = 0;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        prefetch_tensormap(&tm_u);
-        prefetch_tensormap(&tm_v);
-        prefetch_tensormap(&tm_w);
+        prefetch_tensormap(tm_u);
+        prefetch_tensormap(tm_v);
+        prefetch_tensormap(tm_w);
         for (; issued < S && issued < np; ++issued) issue(issued);
     }
 
-    const int r = ty + 1;
-    const int c0 = 4 * lane + PADX;
-    // tile-edge neighbour column: lane 0 needs x = -1, lane 31 needs x = 128;
-    // the other lanes read lane 31's address (a broadcast, no bank conflict)
-    const int ce = (lane == 0) ? PADX - 1 : L::TX + PADX;
-    const int j = TY * by + 1 + ty;
-    const int i0 = 1 + L::TX * bx + 4 * lane;
+    const int r = row + 1;
+    const int c0 = 4 * xl + PADX;
+    // tile-edge neighbour column: the row's first lane needs x = -1, its last
+    // lane x = TX; the other lanes read the last lane's address (a broadcast)
+    const int ce = (xl == 0) ? PADX - 1 : L::TX + PADX;
+    const int j = TY * by + 1 + row;
+    const int i0 = 1 + L::TX * bx + 4 * xl;
     const bool valid = (j <= g.ny) && (i0 <= g.nx);
     const long long row_off = g.origin + (long long)j * g.pj + i0;
     const float tcx = cf.tcx, tcy = cf.tcy;
@@ -311,12 +347,12 @@ __global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
     };
     // x-neighbours of a row vector: value at x = -1 (m) and x = 4 (p)
     auto nbr_m = [&](const float (&x)[4], float edge) {
-        float m = __shfl_up_sync(FULL, x[3], 1);
-        return lane == 0 ? edge : m;
+        float m = __shfl_up_sync(FULL, x[3], 1, LX);
+        return xl == 0 ? edge : m;
     };
     auto nbr_p = [&](const float (&x)[4], float edge) {
-        float p = __shfl_down_sync(FULL, x[0], 1);
-        return lane == 31 ? edge : p;
+        float p = __shfl_down_sync(FULL, x[0], 1, LX);
+        return xl == LX - 1 ? edge : p;
     };
 
     // rows of level kk carried from the previous step (loaded there as level kk+1)
@@ -329,21 +365,19 @@ __global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
         u0[c] = v0[c] = vs[c] = w0[c] = 0.f;
     }
     int waited = 0;   // planes 0..waited-1 are known complete
-    bool aborted = false;
 
-    // One level of the march.  stg / stg_up: ring slots of levels kk and kk+1;
-    // par_up: phase parity of level kk+1's slot.  Returns false on abort.
-    auto level = [&](const int kk, const int stg, const int stg_up, const uint32_t par_up) -> bool {
+    // One level of the march.  Returns false on abort.
+    auto level = [&](const int kk) -> bool {
         const int lp = kk - pb;
         bool ok = true;
-        if (lp == 0) ok = mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);
+        if (lp == 0) ok = mbar_wait_bounded(&bars[slot(0)], parity(0), kWaitLimitNs);
         const bool have_up = (kk + 1 <= pe);
-        if (ok && have_up) ok = mbar_wait_bounded(&bars[stg_up], par_up, kWaitLimitNs);
+        if (ok && have_up) ok = mbar_wait_bounded(&bars[slot(lp + 1)], parity(lp + 1), kWaitLimitNs);
         ok = __all_sync(FULL, ok);
         if (!ok) *abort_flag = 1;
         if (ok) {
             waited = lp + (have_up ? 2 : 1);
-            const T* P = stages + stg * L::STAGE;   // level kk
+            const T* P = stages + slot(lp) * L::STAGE;   // level kk
             if (lp == 0) {
                 ld(P + FU + r * BW + c0, u0, su_in);
                 ld(P + FV + r * BW + c0, v0, sv_in);
@@ -360,7 +394,7 @@ __global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
             float uu[4] = {0, 0, 0, 0}, vu[4] = {0, 0, 0, 0}, vus[4] = {0, 0, 0, 0}, wu[4] = {0, 0, 0, 0};
             float euu = 0.f;
             if (have_up) {
-                const T* Q = stages + stg_up * L::STAGE;
+                const T* Q = stages + slot(lp + 1) * L::STAGE;
                 ld(Q + FU + r * BW + c0, uu, su_in);
                 ld(Q + FV + r * BW + c0, vu, sv_in);
                 ld(Q + FV + (r - 1) * BW + c0, vus, sv_in);
@@ -483,40 +517,51 @@ __global__ void __launch_bounds__(32 * TY, (tma_min_blocks<T, TY, S>()))
         return true;
     };
 
-    // Blocks of S levels with the ring slots known at compile time (plane pb+lp
-    // sits in slot lp % S), then the remaining levels.
-    int kk = pb;
-    for (int blk = 0; PW_TMA_UNROLL && kk + S - 1 <= ke && !aborted; kk += S, ++blk) {
-#pragma unroll
-        for (int q = 0; q < S; ++q)
-            if (!aborted && !level(kk + q, q, (q + 1) % S, (uint32_t)((blk + (q + 1) / S) & 1))) aborted = true;
-    }
-    for (; kk <= ke && !aborted; ++kk) {
-        const int lp = kk - pb;
-        if (!level(kk, lp % S, (lp + 1) % S, (uint32_t)(((lp + 1) / S) & 1))) aborted = true;
-    }
+    bool aborted = false;
+    for (int kk = pb; kk <= ke && !aborted; ++kk)
+        if (!level(kk)) aborted = true;
 
     if (aborted && tid == 0) {
         report_error(err, DEV_TIMEOUT_TMA_WAIT);
         // let the copies still in flight land before the CTA's smem is released
         for (int p = waited; p < issued; ++p)
-            if (!mbar_wait_bounded(&bars[p % S], (p / S) & 1, kDrainLimitNs)) break;
+            if (!mbar_wait_bounded(&bars[slot(p)], parity(p), kDrainLimitNs)) break;
     }
+    return !aborted;
 }
 
-// Instantiated launch shapes: (ty, stages).
-#define PW_TMA_CONFIGS(X) X(4, 4) X(8, 3) X(8, 4) X(8, 6) X(16, 3) X(16, 4)
+// One grid, one tile per CTA: blockIdx = (tile column, tile row, k segment).
+template <typename T, int LX, int TY, int S, bool SCALED, int MODE>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (tma_min_blocks<T, LX, TY, S>()))
+    tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
+               const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
+               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const Scales sc,
+               const CoefDev cf, const float dt, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MarchSmem<T, LX, TY, S> sm(smem_raw);
+    const int bz = blockIdx.z;
+    const int kb = 1 + (int)(((long long)bz * g.nz) / nseg);
+    const int ke = (int)(((long long)(bz + 1) * g.nz) / nseg);
+    if (ke < kb) return;   // empty k segment (the host never launches one)
+    sm.init(threadIdx.y * 32 + threadIdx.x);
+    uint32_t ring = 0;
+    march_tile<T, LX, TY, S, SCALED, MODE>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, sc, cf, dt, blockIdx.x,
+                                           blockIdx.y, kb, ke, ring, err);
+}
 
-template <typename T, int TY, int S, bool SC, int MODE>
+// Instantiated single-grid launch shapes: (lanes per row, rows, stages).
+#define PW_TMA_CONFIGS(X) X(32, 4, 4) X(32, 8, 3) X(32, 8, 4) X(32, 8, 6) X(32, 16, 3) X(16, 4, 4) X(16, 8, 4)
+
+template <typename T, int LX, int TY, int S, bool SC, int MODE>
 static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1,
                                    void* o2, const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
                                    cudaStream_t s) {
-    using L = TmaLayout<T, TY, S>;
-    auto kern = tma_kernel<T, TY, S, SC, MODE>;
+    using L = TmaLayout<T, LX, TY, S>;
+    auto kern = tma_kernel<T, LX, TY, S, SC, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
-    dim3 block(32, TY);
+    dim3 block(32, L::WARPS);
     kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, sc, cf, dt,
                                       err);
     return cudaGetLastError();
@@ -526,11 +571,12 @@ template <typename T, int MODE>
 static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                    const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
                                    const TmaConfig& c, cudaStream_t s) {
-#define PW_DISPATCH(TY_, S_)                                                                                   \
-    if (c.ty == TY_ && c.stages == S_)                                                                         \
-        return scaled                                                                                          \
-                   ? launch_tma_inst<T, TY_, S_, true, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s) \
-                   : launch_tma_inst<T, TY_, S_, false, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s);
+#define PW_DISPATCH(LX_, TY_, S_)                                                                         \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                     \
+        return scaled ? launch_tma_inst<T, LX_, TY_, S_, true, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, \
+                                                                     c.nseg, s)                           \
+                      : launch_tma_inst<T, LX_, TY_, S_, false, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt,    \
+                                                                      err, c.nseg, s);
     PW_TMA_CONFIGS(PW_DISPATCH)
 #undef PW_DISPATCH
     return cudaErrorInvalidConfiguration;

@@ -52,7 +52,7 @@ SIGNATURES = [
     ("pw_create", ctypes.c_int, [ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t), ctypes.POINTER(_VP)]),
     ("pw_destroy", ctypes.c_int, [_VP]),
     ("pw_set_kernel", ctypes.c_int, [_VP, _I32]),
-    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32]),
+    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
@@ -64,6 +64,15 @@ SIGNATURES = [
                                                _dp, _VP]),
     ("pw_sync", ctypes.c_int, [_VP, _VP]),
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
+    ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
+                                       ctypes.POINTER(_VP)]),
+    ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    ("pw_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(_I32)]),
+    ("pw_batch_tendencies", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _FP, _VP]),
+    ("pw_batch_sync", ctypes.c_int, [_VP, _VP]),
+    ("pw_batch_destroy", ctypes.c_int, [_VP]),
     ("pw_last_error", ctypes.c_char_p, []),
     ("pw_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("pw_last_kernel", _I32, [_VP]),
@@ -223,8 +232,8 @@ class PW:
     def set_kernel(self, kind):
         _check(lib().pw_set_kernel(self.h, int(kind)), "pw_set_kernel")
 
-    def set_tma_config(self, ty=0, stages=0, nseg=0):
-        _check(lib().pw_set_tma_config(self.h, int(ty), int(stages), int(nseg)), "pw_set_tma_config")
+    def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0):
+        _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(ty), int(stages), int(nseg)), "pw_set_tma_config")
 
     @property
     def last_kernel(self):
@@ -321,3 +330,62 @@ class PW:
 
     def sync(self, stream=None):
         _check(lib().pw_sync(self.h, _stream_ptr(stream)), "pw_sync")
+
+
+class Batch:
+    """A pw_batch_t: independent grids (one dtype) in one persistent,
+    graph-replayed launch."""
+
+    def __init__(self, grids, coeffs_list):
+        if len(grids) != len(coeffs_list) or not grids:
+            raise ValueError("need one coefficient set per grid")
+        self.grids = list(grids)
+        n = len(grids)
+        self._keep = []
+        cs = (pw_coeffs_t * n)()
+        for q, (g, c) in enumerate(zip(grids, coeffs_list)):
+            arrs = [np.ascontiguousarray(getattr(c, a) if not isinstance(c, dict) else c[a], dtype=np.float64)
+                    for a in ("tzc1", "tzc2", "tzd1", "tzd2")]
+            self._keep.append(arrs)
+            get = (lambda k: c[k]) if isinstance(c, dict) else (lambda k: getattr(c, k))
+            cs[q] = pw_coeffs_t(float(get("tcx")), float(get("tcy")), *[a.ctypes.data_as(_dp) for a in arrs])
+        gs = (pw_grid_t * n)(*[g.c for g in grids])
+        h = ctypes.c_void_p()
+        _check(lib().pw_batch_create(n, gs, cs, ctypes.byref(h)), "pw_batch_create")
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().pw_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, lanes_x=0, ty=0, stages=0, ctas_per_sm=0):
+        _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(ty), int(stages), int(ctas_per_sm)),
+               "pw_batch_set_config")
+
+    def info(self):
+        ni, cells, ctas = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().pw_batch_info(self.h, ctypes.byref(ni), ctypes.byref(cells), ctypes.byref(ctas)),
+               "pw_batch_info")
+        return {"items": ni.value, "cells": cells.value, "ctas": ctas.value}
+
+    def tendencies(self, us, vs, ws, sus, svs, sws, scale=None, stream=None):
+        n = len(self.grids)
+        tabs = []
+        for name, lst in (("u", us), ("v", vs), ("w", ws), ("su", sus), ("sv", svs), ("sw", sws)):
+            if len(lst) != n:
+                raise ValueError(f"{name}: need {n} tensors")
+            tabs.append((_VP * n)(*[_ptr(t, g, name).value for t, g in zip(lst, self.grids)]))
+        sp = _scale_arg(scale)
+        _check(lib().pw_batch_tendencies(self.h, *tabs, sp[0] if sp else None, _stream_ptr(stream)),
+               "pw_batch_tendencies")
+
+    def sync(self, stream=None):
+        _check(lib().pw_batch_sync(self.h, _stream_ptr(stream)), "pw_batch_sync")

@@ -1,0 +1,131 @@
+"""Batched form through the C ABI: many independent grids of uneven sizes in
+one persistent, graph-replayed launch.  Each grid's result is checked against
+the FP64 oracle and against the single-grid k-march kernel of the same tile
+shape (same per-cell arithmetic: bit-identical)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2301_13016_gb300 as pwlib
+from paper_2301_13016_gb300 import autotune, inputs
+from gpu_util import NAN, interior
+
+pytestmark = pytest.mark.gpu
+
+
+def _make_batch(shapes, dtype="f32", seed0=10):
+    grids, coeffs, fields, dev = [], [], [], []
+    for q, (nx, ny, nz) in enumerate(shapes):
+        g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+        c = inputs.make_coeffs(nz, dx=100.0 + q, dy=90.0 + q)
+        f = inputs.random_fields(nx, ny, nz, seeds=(seed0 + 3 * q, seed0 + 3 * q + 1, seed0 + 3 * q + 2))
+        grids.append(g)
+        coeffs.append(c)
+        fields.append(f)
+        dev.append([g.from_dense(x) for x in f])
+    b = pwlib.Batch(grids, coeffs)
+    outs = [[g.alloc(fill=NAN) for _ in range(3)] for g in grids]
+    return b, grids, coeffs, fields, dev, outs
+
+
+def _run(b, dev, outs, scale=None):
+    b.tendencies([d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev],
+                 [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], scale=scale)
+    b.sync()
+
+
+SHAPES = [(32, 40, 8), (384, 36, 5), (100, 17, 12), (64, 64, 3), (260, 9, 20), (36, 300, 6), (128, 4, 4)]
+
+
+@pytest.mark.parametrize("cfg", [(32, 4, 4), (32, 8, 4), (16, 4, 4), (16, 8, 4)])
+def test_batch_matches_oracle_and_single_grid(cfg):
+    b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES)
+    lx, ty, st = cfg
+    b.set_config(lanes_x=lx, ty=ty, stages=st)
+    _run(b, dev, outs)
+    info = b.info()
+    assert info["cells"] == sum(a * c * d for a, c, d in SHAPES)
+    for g, c, f, d, o in zip(grids, coeffs, fields, dev, outs):
+        ref = oracle.tendencies(*[x.numpy() for x in f], c)
+        got = [g.to_dense(t).numpy() for t in o]
+        for x, r in zip(got, ref):
+            assert np.abs(interior(x) - interior(r)).max() <= 1e-5 * np.abs(interior(r)).max()
+            v = x.copy()
+            v[1:-1, 1:-1, 1:-1] = 0
+            assert np.all(np.isnan(v[1:-1, 0])) and np.all(np.isnan(v[1:-1, :, 0]))   # halos untouched
+        h = pwlib.PW(g, c)
+        h.set_tma_config(ty, st, 1, lanes_x=lx)
+        single = [g.alloc(fill=NAN) for _ in range(3)]
+        h.tendencies(*d, *single)
+        h.sync()
+        for x, y in zip(o, single):
+            assert torch.equal(g.view(x)[1:-1, 1:-1, 1:-1], g.view(y)[1:-1, 1:-1, 1:-1])
+
+
+def test_batch_graph_replay_and_pointer_change():
+    b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES[:4])
+    _run(b, dev, outs)
+    first = [[t.clone() for t in o] for o in outs]
+    for o in outs:
+        for t in o:
+            t.fill_(NAN)
+    _run(b, dev, outs)                     # graph replay, same pointers
+    for o, f in zip(outs, first):
+        for x, y in zip(o, f):
+            assert torch.allclose(x, y, rtol=0, atol=0, equal_nan=True)
+    outs2 = [[g.alloc(fill=NAN) for _ in range(3)] for g in grids]
+    _run(b, dev, outs2)                    # new pointers: tables re-uploaded
+    for o, f in zip(outs2, first):
+        for x, y in zip(o, f):
+            assert torch.allclose(x, y, rtol=0, atol=0, equal_nan=True)
+
+
+def test_batch_many_small_grids_bf16():
+    shapes = inputs.batch_shapes(n=48, nxy=(32, 160), nzr=(3, 12))
+    b, grids, coeffs, fields, dev, outs = _make_batch(shapes, dtype="bf16")
+    _run(b, dev, outs)
+    for g, c, d, o in zip(grids, coeffs, dev, outs):
+        qt = [g.to_dense(t).numpy() for t in d]
+        ref = oracle.tendencies(*qt, c)
+        a = oracle.abs_terms(*qt, c)
+        for x, r, at in zip(o, ref, a):
+            got = g.to_dense(x).numpy()
+            err = np.abs(interior(got) - interior(r))
+            assert np.all(err <= 2.0 ** -8 * np.abs(interior(r)) + 2.0 ** -19 * interior(at) + 1e-30)
+
+
+def test_batch_rejects_bad_pointers_and_layouts():
+    b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES[:2])
+    bad = torch.empty(grids[0].alloc_elems + 1, device="cuda")[1:]
+    with pytest.raises(pwlib.PwError) as e:
+        b.tendencies([bad, dev[1][0]], [d[1] for d in dev], [d[2] for d in dev],
+                     [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    assert e.value.status == pwlib.PW_ERR_ALIGN
+    g_odd = pwlib.Grid(30, 8, 4)        # nx not a multiple of 4
+    with pytest.raises(pwlib.PwError) as e:
+        pwlib.Batch([g_odd], [inputs.make_coeffs(4)])
+    assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES)
+    flds = ([d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev],
+            [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    path = str(tmp_path / "tune.json")
+    cfg, times = autotune.tune_batch(b, flds, cache_path=path, reps=2)
+    assert len(times) >= 4 and cfg in autotune.BATCH_CANDIDATES
+    cfg2, _ = autotune.tune_batch(b, flds, cache_path=path)
+    assert cfg2 == cfg
+    _run(b, dev, outs)
+    for g, c, f, o in zip(grids, coeffs, fields, outs):
+        ref = oracle.tendencies(*[x.numpy() for x in f], c)
+        for x, r in zip(o, ref):
+            got = g.to_dense(x).numpy()
+            assert np.abs(interior(got) - interior(r)).max() <= 1e-5 * np.abs(interior(r)).max()
+    # single grid
+    g, c, d = grids[1], coeffs[1], dev[1]
+    h = pwlib.PW(g, c)
+    s = [g.alloc() for _ in range(3)]
+    gcfg, gt = autotune.tune_grid(h, (*d, *s), cache_path=path, reps=2)
+    assert gcfg in autotune.GRID_CANDIDATES and len(gt) >= 4

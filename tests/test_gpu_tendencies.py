@@ -34,6 +34,16 @@ def test_parity_random(shape, kernel):
     assert max(rel_errs(got, [r.astype(np.float64) for r in ref32])) <= TOL
 
 
+@pytest.mark.parametrize("shape", [(64, 64, 64), (388, 37, 5), (36, 12, 3)], ids=["64", "388", "36"])
+def test_parity_narrow_tiles(shape):
+    c, f, g, h, dev, outs = setup(*shape)
+    h.set_kernel(2)
+    h.set_tma_config(4, 4, 0, lanes_x=16)
+    run(h, dev, outs)
+    ref64 = oracle.tendencies(*[x.numpy() for x in f], c)
+    assert max(rel_errs(dense_out(g, outs), ref64)) <= TOL
+
+
 @pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
 def test_parity_smooth(kernel):
     c, f, g, h, dev, outs = setup(64, 64, 64, smooth=True)
@@ -68,18 +78,18 @@ def test_k_segments_bitwise_and_configs_agree():
     c, f, g, h, dev, outs = setup(256, 24, 20)
     h.set_kernel(2)
     results = {}
-    for ty, st in ((4, 4), (8, 3), (8, 4), (8, 6), (16, 3), (16, 4)):
+    for lx, ty, st in ((32, 4, 4), (32, 8, 3), (32, 8, 4), (32, 8, 6), (32, 16, 3), (16, 4, 4), (16, 8, 4)):
         for nseg in (1, 2, 3, 10):
-            h.set_tma_config(ty, st, nseg)
+            h.set_tma_config(ty, st, nseg, lanes_x=lx)
             for o in outs:
                 o.fill_(NAN)
             run(h, dev, outs)
-            results[(ty, st, nseg)] = dense_out(g, outs)
-    for (ty, st, nseg), r in results.items():
-        base = results[(ty, st, 1)]
+            results[(lx, ty, st, nseg)] = dense_out(g, outs)
+    for (lx, ty, st, nseg), r in results.items():
+        base = results[(lx, ty, st, 1)]
         for x, y in zip(r, base):
-            assert np.array_equal(x, y, equal_nan=True), (ty, st, nseg)     # same code path per cell
-        ref = results[(8, 4, 1)]
+            assert np.array_equal(x, y, equal_nan=True), (lx, ty, st, nseg)     # same code path per cell
+        ref = results[(32, 4, 4, 1)]
         for x, y in zip(r, ref):
             assert np.abs(interior(x) - interior(y)).max() <= 1e-6 * np.abs(interior(y)).max()
 
