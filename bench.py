@@ -35,7 +35,9 @@ METRIC = "PW advection Gcell/s & % of HBM peak; FP32 vs BF16-stored at stated er
 BYTES_PER_CELL_F32 = 24          # read u, v, w + write su, sv, sw (4 bytes each)
 FLOPS_PER_CELL = 63              # 21 useful FLOPs per field (Sec. 4 op structure)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", "pw_tend.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
+                  for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
+FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "precision", "batch", "adjoint", "latency64"]
 
 
 def parse():
@@ -47,6 +49,8 @@ def parse():
     p.add_argument("--workload", choices=["2048", "512"], default="2048")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--form", choices=FORMS, default="tend",
+                   help="tend (default: the headline FP32 tendency benchmark) or another form of the path")
     return p.parse_args()
 
 
@@ -101,8 +105,11 @@ def measured_peak():
 
 
 def kernel_source_hash():
-    with open(KERNEL_SOURCE, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
@@ -307,14 +314,322 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other forms of the path (one JSON line each, rank 0, N = 1): each is timed
+# beside the plain FP32 tendency kernel on the same GPU in the same process.
+
+def _events_ms(fn, n, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def _fp32_reference_rate(nx, ny, nz, steps, stream):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, inputs.make_coeffs(nz))
+    dense = inputs.random_fields(nx, ny, nz, device="cuda")
+    dev = [g.from_dense(x) for x in dense]
+    del dense
+    outs = [g.alloc() for _ in range(3)]
+    f = lambda: h.tendencies(*dev, *outs, stream=stream)
+    for _ in range(5):
+        f()
+    ms = _events_ms(f, steps, stream)
+    h.sync(stream)
+    del dev, outs
+    torch.cuda.empty_cache()
+    return g.cells / (ms / 1e3) / 1e9
+
+
+def _form_line(args, form, metric, value, unit, config, extra):
+    line = {"form": form, "metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "config": config}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def form_tend_lowp(args, dtype):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs, precision
+    nx = ny = 2048
+    nz = 64
+    stream = torch.cuda.current_stream()
+    ref = _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    h = pwlib.PW(g, c)
+    dense = inputs.random_fields(nx, ny, nz, device="cuda")
+    sc = precision.suggest_scales([float(x.abs().max()) for x in dense], c, dtype)
+    dev = [g.from_dense(x, scale=s) for x, s in zip(dense, sc[:3])]
+    del dense
+    outs = [g.alloc() for _ in range(3)]
+    f = lambda: h.tendencies(*dev, *outs, scale=sc, stream=stream)
+    for _ in range(args.warmup):
+        f()
+    ms = _events_ms(f, args.steps, stream)
+    h.sync(stream)
+    val = g.cells / (ms / 1e3) / 1e9
+    peak, kind = measured_peak()
+    achieved = 12 * g.cells / (ms / 1e3) / 1e9
+    _form_line(args, f"tend-{dtype}", f"PW tendencies Gcell/s, {dtype.upper()} storage (FP32 arithmetic)", val,
+               "Gcell/s", {"workload": f"{nx}x{ny}x{nz} random 10*N(0,1), {dtype} storage, per-field power-of-two scales",
+                           "scales": list(sc)},
+               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref, "fp32_form_gcells": ref,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": 12},
+                "gpu_launches": args.steps})
+
+
+def form_step(args, dtype):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs, precision
+    nx = ny = 2048
+    nz = 64
+    stream = torch.cuda.current_stream()
+    ref = _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    h = pwlib.PW(g, c)
+    dense = inputs.smooth_fields(nx, ny, nz, w_zero=True, device="cuda")
+    sc = precision.suggest_scales([max(float(x.abs().max()), 1.0) for x in dense], c, dtype)[:3]
+    q = [g.from_dense(x, scale=s) for x, s in zip(dense, sc)]
+    del dense
+    tmp = [g.alloc() for _ in range(3)]
+    nsteps = args.steps if args.steps % 2 == 0 else args.steps + 1   # even: no final copy-back
+    f = lambda: h.step(*q, *tmp, 0.0, nsteps, scale=sc, stream=stream)
+    h.step(*q, *tmp, 0.0, 2, scale=sc, stream=stream)
+    ms = _events_ms(f, 1, stream) / nsteps
+    h.sync(stream)
+    val = g.cells / (ms / 1e3) / 1e9
+    es = 4 if dtype == "f32" else 2
+    peak, kind = measured_peak()
+    achieved = 6 * es * g.cells / (ms / 1e3) / 1e9
+    _form_line(args, "step" if dtype == "f32" else f"step-{dtype}",
+               f"PW fused forward-Euler step, Gcell-steps/s, {dtype.upper()} state", val, "Gcell-steps/s",
+               {"workload": f"{nx}x{ny}x{nz} smooth field (w = 0 initially), {nsteps} fused steps per call "
+                            "(dt = 0 keeps the state fixed for timing)", "scales": list(sc)},
+               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_tend_form": val / ref, "fp32_tend_gcells": ref,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell_step": 6 * es},
+                "gpu_launches": nsteps + 3})
+
+
+def form_precision(args):
+    """100 fused Euler steps, dt = 1 s, on a smooth field with w = 0 initially
+    and on the random field until divergence: max|err|/max|ref| per field
+    against the FP64 oracle's rollout every 10 steps, FP32 / BF16 / FP16 state."""
+    import numpy as np
+    import oracle
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs, precision
+    nx = ny = 256
+    nz = 64
+    nsteps, every = 100, 10
+    c = inputs.make_coeffs(nz)
+    out = {}
+    for field in ("smooth_w0", "random"):
+        dense = (inputs.smooth_fields(nx, ny, nz, w_zero=True) if field == "smooth_w0"
+                 else inputs.random_fields(nx, ny, nz))
+        ref = [x.numpy().astype(np.float64) for x in dense]
+        refs = []
+        for n in range(0, nsteps, every):
+            ref = list(oracle.step(*ref, c, 1.0, every))
+            refs.append(ref)
+        res = {}
+        for dtype in ("f32", "bf16", "f16"):
+            g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+            h = pwlib.PW(g, c)
+            sc = precision.suggest_scales([max(float(x.abs().max()), 1.0) for x in dense], c, dtype)[:3]
+            q = [g.from_dense(x, scale=s) for x, s in zip(dense, sc)]
+            tmp = [g.alloc() for _ in range(3)]
+            errs = []
+            for n in range(nsteps // every):
+                h.step(*q, *tmp, 1.0, every, scale=sc)
+                h.sync()
+                got = [g.to_dense(t, s).numpy() for t, s in zip(q, sc)]
+                r = refs[n]
+                umax = np.abs(r[0][1:-1, 1:-1, 1:-1]).max()
+                row = {"step": (n + 1) * every, "max_ref": float(umax)}
+                for name, a, b in zip("uvw", got, r):
+                    d = np.abs(a[1:-1, 1:-1, 1:-1] - b[1:-1, 1:-1, 1:-1])
+                    den = max(np.abs(b[1:-1, 1:-1, 1:-1]).max(), umax if name == "w" else 0.0)
+                    row[name] = float(d.max() / den) if np.isfinite(d).all() and den > 0 else None
+                errs.append(row)
+                if not np.isfinite(umax) or umax > 1e3 * 10:
+                    break
+            res[dtype] = errs
+        out[field] = res
+    _form_line(args, "precision", "max|err|/max|ref| vs FP64 oracle per 10 steps, 100 fused Euler steps", None,
+               "relative error", {"workload": f"{nx}x{ny}x{nz}, dt = 1 s; smooth field with w = 0 initially, and "
+                                              "the random 10*N(0,1) field (diverges: errors reported until then)"},
+               {"errors": out})
+
+
+def form_batch(args):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import autotune, inputs
+    stream = torch.cuda.current_stream()
+    ref = _fp32_reference_rate(2048, 2048, 64, 50, stream)
+    shapes = inputs.batch_shapes()
+    grids, coeffs, dev, outs = [], [], [], []
+    for q, (nx, ny, nz) in enumerate(shapes):
+        g = pwlib.Grid(nx, ny, nz)
+        c = inputs.make_coeffs(nz)
+        d = inputs.random_fields(nx, ny, nz, device="cuda", seeds=(10 + 3 * q, 11 + 3 * q, 12 + 3 * q))
+        grids.append(g)
+        coeffs.append(c)
+        dev.append([g.from_dense(x) for x in d])
+        outs.append([g.alloc(fill=None) for _ in range(3)])
+        del d
+    b = pwlib.Batch(grids, coeffs)
+    flds = ([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev],
+            [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    t0 = time.perf_counter()
+    cfg, times = autotune.tune_batch(b, flds, reps=3, force=True,
+                                     cache_path=os.path.join(ROOT, "gpurun_out", "tune_batch.json")
+                                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    tune_s = time.perf_counter() - t0
+    f = lambda: b.tendencies(*flds, stream=stream)
+    for _ in range(args.warmup):
+        f()
+    ms = _events_ms(f, args.steps, stream)
+    b.sync(stream)
+    info = b.info()
+    val = info["cells"] / (ms / 1e3) / 1e9
+    peak, kind = measured_peak()
+    achieved = 24 * info["cells"] / (ms / 1e3) / 1e9
+    _form_line(args, "batch", "PW tendencies Gcell/s, 512 independent grids in one persistent graph-replayed launch",
+               val, "Gcell/s", {"workload": "512 grids, nx, ny ~ U{32..384 step 4}, nz ~ U{32..128} (seed 2304), "
+                                            "FP32, random 10*N(0,1)", "cells": info["cells"],
+                                "items": info["items"], "ctas": info["ctas"], "tile": cfg},
+               {"dtype": "f32", "ms_per_step": ms, "vs_fp32_form": val / ref, "fp32_form_gcells": ref,
+                "autotune_s": tune_s, "autotune_ms": times,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": 24},
+                "gpu_launches": args.steps})
+
+
+def form_adjoint(args):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs
+    from paper_2301_13016_gb300.autograd import rollout
+    nx = ny = 512
+    nz = 64
+    nsteps, every, dt = 20, 5, 1.0
+    stream = torch.cuda.current_stream()
+    ref = _fp32_reference_rate(nx, ny, nz, 50, stream)
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, c)
+    f = inputs.smooth_fields(nx, ny, nz, w_zero=True, device="cuda")
+    ut = inputs.target_field(nx, ny, nz, device="cuda")
+    q0 = [g.from_dense(x).requires_grad_(True) for x in f]
+
+    def run():
+        for t in q0:
+            t.grad = None
+        uT, vT, wT = rollout(*q0, h, dt, nsteps, every)
+        d = g.view(uT)[1:-1, 1:-1, 1:-1].double() - ut[1:-1, 1:-1, 1:-1].double()
+        L = 0.5 * (d * d).sum()
+        L.backward()
+        return L
+
+    run()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = max(1, min(args.steps, 5))
+    fwd_ms = bwd_ms = 0.0
+    for _ in range(reps):
+        for t in q0:
+            t.grad = None
+        e[0].record(stream)
+        uT, vT, wT = rollout(*q0, h, dt, nsteps, every)
+        d = g.view(uT)[1:-1, 1:-1, 1:-1].double() - ut[1:-1, 1:-1, 1:-1].double()
+        L = 0.5 * (d * d).sum()
+        e[1].record(stream)
+        L.backward()
+        e[2].record(stream)
+        e[2].synchronize()
+        fwd_ms += e[0].elapsed_time(e[1]) / reps
+        bwd_ms += e[1].elapsed_time(e[2]) / reps
+    # the adjoint kernel alone (one reverse step)
+    gs = [g.from_dense(inputs.target_field(nx, ny, nz, std=1.0, seed=2306 + n, device="cuda")) for n in range(3)]
+    g2 = [g.alloc() for _ in range(3)]
+    qs = [t.detach().clone() for t in q0]
+    h.step(*qs, *g2, dt, 0)
+    adj = lambda: h.adjoint(*qs, *gs, *g2, alpha=dt, flags=pwlib.PW_ADJ_PERIODIC | pwlib.PW_ADJ_ADD_LAMBDA,
+                            stream=stream)
+    adj()
+    adj_ms = _events_ms(adj, 20, stream)
+    cell_steps = g.cells * nsteps
+    peak, kind = measured_peak()
+    adj_gbs = 36 * g.cells / (adj_ms / 1e3) / 1e9
+    _form_line(args, "adjoint", "PW adjoint rollout: Gcell-steps/s of forward + backward (checkpointed)",
+               cell_steps / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "Gcell-steps/s",
+               {"workload": f"{nx}x{ny}x{nz} FP32, {nsteps} Euler steps dt = {dt}, checkpoint every {every}, "
+                            "loss 0.5*sum((u_T - u_target)^2), u_target ~ N(0, 10^2) (seed 2305)"},
+               {"dtype": "f32", "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+                "backward_gcell_steps": cell_steps / (bwd_ms / 1e3) / 1e9,
+                "adjoint_kernel_ms": adj_ms, "adjoint_kernel_gcells": g.cells / (adj_ms / 1e3) / 1e9,
+                "vs_fp32_form": (g.cells / (adj_ms / 1e3) / 1e9) / ref, "fp32_form_gcells": ref,
+                "roofline": {"bound": "hbm", "kernel": "adjoint_gather_kernel", "achieved": adj_gbs, "peak": peak,
+                             "unit": "GB/s", "frac": adj_gbs / peak, "peak_kind": kind, "bytes_per_cell": 36}})
+
+
+def form_latency64(args):
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs
+    nx = ny = nz = 64
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, c)
+    dev = [g.from_dense(x) for x in inputs.random_fields(nx, ny, nz)]
+    outs = [g.alloc() for _ in range(3)]
+    s = torch.cuda.Stream()
+    res = {}
+    for lx, ty in ((32, 4), (16, 4)):
+        h.set_tma_config(ty, 4, 0, lanes_x=lx)
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                h.tendencies(*dev, *outs, stream=s)
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        n_in = 100
+        with torch.cuda.graph(graph, stream=s):
+            for _ in range(n_in):
+                h.tendencies(*dev, *outs, stream=s)
+        graph.replay()
+        torch.cuda.synchronize()
+        ms = _events_ms(graph.replay, 20, torch.cuda.current_stream()) / n_in
+        direct = _events_ms(lambda: h.tendencies(*dev, *outs), 200, torch.cuda.current_stream())
+        res[f"lanes{lx}_ty{ty}"] = {"graph_us_per_call": ms * 1e3, "stream_us_per_call": direct * 1e3}
+    best = min(v["graph_us_per_call"] for v in res.values())
+    _form_line(args, "latency64", "PW tendencies latency per call, 64^3 FP32 (graph replay)", best, "us",
+               {"workload": "64x64x64 FP32 random 10*N(0,1); L2-resident, launch-bound (not a roofline point)"},
+               {"dtype": "f32", "higher_is_better": False, "shapes": res, "gcells_at_best": g.cells / best / 1e3})
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
-        else:
+        elif args.form == "tend":
             run_ours(args, rank, world, local)
+        elif rank == 0:
+            {"tend-bf16": lambda: form_tend_lowp(args, "bf16"), "tend-f16": lambda: form_tend_lowp(args, "f16"),
+             "step": lambda: form_step(args, "f32"), "step-bf16": lambda: form_step(args, "bf16"),
+             "precision": lambda: form_precision(args), "batch": lambda: form_batch(args),
+             "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args)}[args.form]()
     finally:
         if world > 1:
             import torch.distributed as dist

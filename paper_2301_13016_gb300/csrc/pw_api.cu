@@ -225,6 +225,20 @@ pw_status_t internal_fail(pw_status_t s, const char* fmt, ...) {
 
 pw_status_t internal_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
+cudaError_t set_smem_attr_once_impl(const void* kern, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> done;   // (kernel, device)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first == kern && d.second == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back(kern, dev);
+    return e;
+}
+
 bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms) {
     if (!h) return false;
     *g = h->grid;

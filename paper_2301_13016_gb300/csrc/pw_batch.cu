@@ -68,7 +68,7 @@ static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, c
                               cudaStream_t s) {
     using L = TmaLayout<T, LX, TY, S>;
     auto kern = tma_batch_kernel<T, LX, TY, S, SC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
     kern<<<ctas, dim3(32, L::WARPS), L::SMEM, s>>>(grids, maps, items, n_items, counter, sc, err);

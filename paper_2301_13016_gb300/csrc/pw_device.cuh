@@ -158,6 +158,14 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device)
+// (a host-side attribute call, kept out of the per-launch path).
+cudaError_t set_smem_attr_once_impl(const void* kern, int bytes);
+template <typename K>
+__host__ inline cudaError_t set_smem_attr_once(K kern, int bytes) {
+    return set_smem_attr_once_impl(reinterpret_cast<const void*>(kern), bytes);
+}
+
 __device__ __forceinline__ void report_error(int* flag, int code) {
     if (flag) atomicCAS(flag, DEV_OK, code);
 }

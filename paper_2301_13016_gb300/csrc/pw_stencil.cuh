@@ -558,7 +558,7 @@ static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* 
                                    cudaStream_t s) {
     using L = TmaLayout<T, LX, TY, S>;
     auto kern = tma_kernel<T, LX, TY, S, SC, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
     dim3 block(32, L::WARPS);
