@@ -196,8 +196,14 @@ pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void 
  * output cells wrap around, and g is the sensitivity with respect to the
  * interior values (the halo contributions folded onto their images); g is
  * written on the interior only.  Cells of g not listed are not written.
+ * In periodic mode, when the layout and pointers qualify for the TMA
+ * kernels (and pw_set_kernel did not ask for the generic one), the TMA
+ * k-march adjoint runs and the lateral halos of lsu, lsv, lsw are first
+ * overwritten with their periodic images (their halo values carry no
+ * meaning in this mode).  Otherwise the generic gather kernel runs; it skips
+ * a term whose sensitivity is exactly 0.
  * FP32 storage only (PW_ERR_UNSUPPORTED otherwise).  g must not alias any
- * input.  A term whose sensitivity is exactly 0 is skipped.
+ * input.  pw_last_kernel reports 1 (generic) or 2 (TMA).
  */
 pw_status_t pw_adjoint(pw_handle_t h, const void *u, const void *v, const void *w,
                        const void *lsu, const void *lsv, const void *lsw,

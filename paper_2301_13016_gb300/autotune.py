@@ -129,3 +129,50 @@ def tune_grid(handle, fields, candidates=None, warmup=2, reps=5, cache_path=None
     handle.set_tma_config(**best)
     _store(cache_path, key, {"config": best, "times": times})
     return best, times
+
+
+def main(argv=None):
+    """python -m paper_2301_13016_gb300.autotune NX NY NZ [--dtype f32] [--json]
+    Times every single-grid launch shape on a seeded random grid (tendencies
+    and fused steps) and prints one JSON line."""
+    import argparse
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs, precision
+
+    p = argparse.ArgumentParser()
+    p.add_argument("nx", type=int)
+    p.add_argument("ny", type=int)
+    p.add_argument("nz", type=int)
+    p.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--tag", default="")
+    a = p.parse_args(argv)
+    c = inputs.make_coeffs(a.nz)
+    g = pwlib.Grid(a.nx, a.ny, a.nz, dtype=a.dtype)
+    h = pwlib.PW(g, c)
+    dense = inputs.random_fields(a.nx, a.ny, a.nz, device="cuda")
+    sc = precision.suggest_scales([float(x.abs().max()) for x in dense], c, a.dtype)
+    dev = [g.from_dense(x, scale=s) for x, s in zip(dense, sc[:3])]
+    del dense
+    outs = [g.alloc() for _ in range(3)]
+    tmp = [g.alloc() for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    res = {}
+    seen = set()
+    for cand in GRID_CANDIDATES:
+        key = (cand["lanes_x"], cand["ty"], cand["stages"])
+        if key in seen:
+            continue
+        seen.add(key)
+        h.set_tma_config(cand["ty"], cand["stages"], 0, lanes_x=cand["lanes_x"])
+        ms_t = _time(lambda: h.tendencies(*dev, *outs, scale=sc, stream=stream), 3, a.reps, stream)
+        ms_s = _time(lambda: h.step(*dev, *tmp, 0.0, 2, scale=sc[:3], stream=stream), 2, a.reps, stream) / 2
+        h.sync(stream)
+        res[f"lanes{key[0]}_ty{key[1]}_s{key[2]}"] = {"tend_gcells": g.cells / ms_t / 1e6,
+                                                      "step_gcells": g.cells / ms_s / 1e6}
+    print(json.dumps({"grid": [a.nx, a.ny, a.nz], "dtype": a.dtype, "tag": a.tag, "device": _device_key(),
+                      "shapes": res}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,243 @@ __global__ void adjoint_gather_kernel(const GridDev g, const AdjArgs a, const Co
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA k-march adjoint (periodic mode, FP32).  A CTA owns 128 x TY interior
+// columns; one thread issues 3D TMA copies of the u, v, w and lsu, lsv, lsw
+// planes (tile plus one-cell halo) into a ring of S slots, keeping levels
+// k-1, k, k+1 resident while S-3 more are in flight.  Thread (lane, ty)
+// gathers 4 cells x = lane + 32q of row ty: every shared-memory access of a
+// warp touches 32 consecutive words (no bank conflicts, no shuffles).  The
+// halos of u, v, w and of l must hold periodic images.
+constexpr int kAdjTX = 128;
+constexpr int kAdjPAD = 4;                       // 16-byte granule of FP32
+constexpr int kAdjBW = kAdjTX + 2 * kAdjPAD;
+
+template <int TY, int S>
+struct AdjLayout {
+    static constexpr int ROWS = TY + 2;
+    static constexpr int FIELD_RAW = kAdjBW * ROWS;
+    static constexpr int FIELD = ((FIELD_RAW * 4 + 127) / 128) * 32;   // floats, 128-byte multiple
+    static constexpr int STAGE = 6 * FIELD;
+    static constexpr uint32_t TX_BYTES = 6u * FIELD_RAW * 4u;
+    static constexpr size_t SMEM = (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
+};
+
+struct AdjMaps {
+    CUtensorMap m[6];   // u, v, w, lsu, lsv, lsw
+};
+
+template <int TY, int S>
+__global__ void __launch_bounds__(32 * TY)
+    adjoint_tma_kernel(const __grid_constant__ AdjMaps maps, float* __restrict__ gu, float* __restrict__ gv,
+                       float* __restrict__ gw, const GridDev g, const int ox, const int nseg, const CoefDev cf,
+                       const float alpha, const int accumulate, const int add_lambda, int* __restrict__ err) {
+    using L = AdjLayout<TY, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stages = reinterpret_cast<float*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * L::STAGE * 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S);
+
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+    const int nz = g.nz, nzp2 = nz + 2;
+    const int kb = 1 + (int)(((long long)blockIdx.z * nz) / nseg);
+    const int ke = (int)(((long long)(blockIdx.z + 1) * nz) / nseg);
+    if (ke < kb) return;
+    const int pb = max(kb - 1, 1), pe = min(ke + 1, nz), np = pe - pb + 1;
+    const int X0 = ox + 1 + kAdjTX * blockIdx.x - kAdjPAD;
+    const int Y0 = TY * blockIdx.y + g.halo - 1;
+
+    auto issue = [&](int p) {
+        const int s = p % S;
+        float* dst = stages + s * L::STAGE;
+        mbar_arrive_expect_tx(&bars[s], L::TX_BYTES);
+        for (int f = 0; f < 6; ++f) tma_load_3d(dst + f * L::FIELD, &maps.m[f], X0, Y0, pb + p, &bars[s]);
+    };
+    int issued = 0;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int f = 0; f < 6; ++f) prefetch_tensormap(&maps.m[f]);
+        for (; issued < S && issued < np; ++issued) issue(issued);
+    }
+
+    const float* tzc1 = cf.tz;
+    const float* tzc2 = cf.tz + nzp2;
+    const float* tzd1 = cf.tz + 2 * nzp2;
+    const float* tzd2 = cf.tz + 3 * nzp2;
+    const float tcx = cf.tcx, tcy = cf.tcy;
+    const int r = ty + 1;
+    const int J = TY * blockIdx.y + 1 + ty;
+    int waited = 0;
+    bool aborted = false;
+
+    for (int K = kb; K <= ke; ++K) {
+        const int lp = K - pb;
+        bool ok = true;
+        const int need_hi = (K + 1 <= pe) ? lp + 1 : lp;
+        for (int p = (K == kb ? 0 : need_hi); p <= need_hi && ok; ++p)
+            ok = mbar_wait_bounded(&bars[p % S], (uint32_t)((p / S) & 1), kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) *abort_flag = 1;
+        if (ok) {
+            waited = need_hi + 1;
+            const float* Pm = stages + ((lp - 1 + S) % S) * L::STAGE;   // level K-1 (valid when K-1 >= pb)
+            const float* P0 = stages + (lp % S) * L::STAGE;             // level K
+            const float* Pp = stages + ((lp + 1) % S) * L::STAGE;       // level K+1 (valid when K+1 <= pe)
+            const bool has_m = (K - 1 >= 1), has_p = (K + 1 <= nz);
+            // sensitivities exist at output levels 2..nz (su, sv; upper terms
+            // 2..nz-1) and 2..nz-1 (sw)
+            const bool lu0 = (K >= 2), lum = (K - 1 >= 2), lup = (K + 1 <= nz);
+            const bool lut0 = (K >= 2 && K <= nz - 1), lutm = (K - 1 >= 2 && K - 1 <= nz - 1);
+            const bool lw0 = (K >= 2 && K <= nz - 1), lwm = (K - 1 >= 2 && K - 1 <= nz - 1),
+                       lwp = (K + 1 >= 2 && K + 1 <= nz - 1);
+            const float c1p = has_p ? tzc1[K + 1] : 0.f, c2m = has_m ? tzc2[K - 1] : 0.f, c2 = tzc2[K];
+            const float d1p = has_p ? tzd1[K + 1] : 0.f, d1 = tzd1[K], d2 = tzd2[K];
+            const float d2m = has_m ? tzd2[K - 1] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = lane + 32 * q;
+                const int c = x + kAdjPAD;
+                const int I = 1 + kAdjTX * blockIdx.x + x;
+                // field f at (level K+dk, row r+dj, column c+di)
+                auto A = [&](const float* P, int f, int dj, int di) { return P[f * L::FIELD + (r + dj) * kAdjBW + c + di]; };
+                auto U0 = [&](int dj, int di) { return A(P0, 0, dj, di); };
+                auto V0 = [&](int dj, int di) { return A(P0, 1, dj, di); };
+                auto W0 = [&](int dj, int di) { return A(P0, 2, dj, di); };
+                auto Um = [&](int dj, int di) { return A(Pm, 0, dj, di); };
+                auto Vm = [&](int dj, int di) { return A(Pm, 1, dj, di); };
+                auto Wm = [&](int dj, int di) { return A(Pm, 2, dj, di); };
+                auto Up = [&](int dj, int di) { return A(Pp, 0, dj, di); };
+                auto Vp = [&](int dj, int di) { return A(Pp, 1, dj, di); };
+                auto Wp = [&](int dj, int di) { return A(Pp, 2, dj, di); };
+                auto LU0 = [&](int dj, int di) { return lu0 ? A(P0, 3, dj, di) : 0.f; };
+                auto LV0 = [&](int dj, int di) { return lu0 ? A(P0, 4, dj, di) : 0.f; };
+                auto LW0 = [&](int dj, int di) { return lw0 ? A(P0, 5, dj, di) : 0.f; };
+                auto LUT0 = [&](int dj, int di) { return lut0 ? A(P0, 3, dj, di) : 0.f; };
+                auto LVT0 = [&](int dj, int di) { return lut0 ? A(P0, 4, dj, di) : 0.f; };
+
+                float ru = 0.f, rv = 0.f, rw = 0.f;
+                // ---- gu
+                ru += tcx * LU0(0, 1) * (U0(0, 1) + 2.f * U0(0, 0));
+                ru += tcx * LU0(0, 0) * U0(0, -1);
+                ru -= tcx * LU0(0, -1) * (U0(0, -1) + 2.f * U0(0, 0));
+                ru -= tcx * LU0(0, 0) * U0(0, 1);
+                ru += tcy * LU0(1, 0) * (V0(0, 0) + V0(0, 1));
+                ru -= tcy * LU0(-1, 0) * (V0(-1, 0) + V0(-1, 1));
+                if (has_p && lup) ru += c1p * A(Pp, 3, 0, 0) * (W0(0, 0) + W0(0, 1));
+                if (has_m && lutm) ru -= c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1));
+                ru += tcx * LV0(0, 1) * V0(0, 0);
+                ru += tcx * LV0(-1, 1) * V0(-1, 0);
+                ru -= tcx * LV0(0, 0) * V0(0, 1);
+                ru -= tcx * LV0(-1, 0) * V0(-1, 1);
+                ru += tcx * LW0(0, 1) * W0(0, 0);
+                ru -= tcx * LW0(0, 0) * W0(0, 1);
+                if (has_m && lwm) {
+                    ru += tcx * A(Pm, 5, 0, 1) * Wm(0, 0);
+                    ru -= tcx * A(Pm, 5, 0, 0) * Wm(0, 1);
+                }
+                // ---- gv
+                rv += tcy * LU0(1, 0) * U0(0, 0);
+                rv += tcy * LU0(1, -1) * U0(0, -1);
+                rv -= tcy * LU0(0, 0) * U0(1, 0);
+                rv -= tcy * LU0(0, -1) * U0(1, -1);
+                rv += tcx * LV0(0, 1) * (U0(0, 0) + U0(1, 0));
+                rv -= tcx * LV0(0, -1) * (U0(0, -1) + U0(1, -1));
+                rv += tcy * LV0(1, 0) * (V0(1, 0) + 2.f * V0(0, 0));
+                rv += tcy * LV0(0, 0) * V0(-1, 0);
+                rv -= tcy * LV0(-1, 0) * (V0(-1, 0) + 2.f * V0(0, 0));
+                rv -= tcy * LV0(0, 0) * V0(1, 0);
+                if (has_p && lup) rv += c1p * A(Pp, 4, 0, 0) * (W0(0, 0) + W0(1, 0));
+                if (has_m && lutm) rv -= c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0));
+                rv += tcy * LW0(1, 0) * W0(0, 0);
+                rv -= tcy * LW0(0, 0) * W0(1, 0);
+                if (has_m && lwm) {
+                    rv += tcy * A(Pm, 5, 1, 0) * Wm(0, 0);
+                    rv -= tcy * A(Pm, 5, 0, 0) * Wm(1, 0);
+                }
+                // ---- gw
+                if (has_p) {
+                    if (lup) {
+                        rw += c1p * A(Pp, 3, 0, 0) * U0(0, 0);
+                        rw += c1p * A(Pp, 3, 0, -1) * U0(0, -1);
+                        rw += c1p * A(Pp, 4, 0, 0) * V0(0, 0);
+                        rw += c1p * A(Pp, 4, -1, 0) * V0(-1, 0);
+                    }
+                    rw -= c2 * LUT0(0, 0) * Up(0, 0);
+                    rw -= c2 * LUT0(0, -1) * Up(0, -1);
+                    rw -= c2 * LVT0(0, 0) * Vp(0, 0);
+                    rw -= c2 * LVT0(-1, 0) * Vp(-1, 0);
+                    rw += tcx * LW0(0, 1) * (U0(0, 0) + Up(0, 0));
+                    rw -= tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1));
+                    rw += tcy * LW0(1, 0) * (V0(0, 0) + Vp(0, 0));
+                    rw -= tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0));
+                    if (lwp) rw += d1p * A(Pp, 5, 0, 0) * (Wp(0, 0) + 2.f * W0(0, 0));
+                    rw -= d2 * LW0(0, 0) * Wp(0, 0);
+                }
+                if (has_m) {
+                    rw += d1 * LW0(0, 0) * Wm(0, 0);
+                    if (lwm) rw -= d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0));
+                }
+
+                if (J <= g.ny && I <= g.nx) {
+                    const long long o = g.origin + (long long)K * g.pk + (long long)J * g.pj + I;
+                    float bu = 0.f, bv = 0.f, bw = 0.f;
+                    if (accumulate) {
+                        bu = gu[o];
+                        bv = gv[o];
+                        bw = gw[o];
+                    } else if (add_lambda) {
+                        bu = A(P0, 3, 0, 0);
+                        bv = A(P0, 4, 0, 0);
+                        bw = A(P0, 5, 0, 0);
+                    }
+                    gu[o] = fmaf(alpha, ru, bu);
+                    gv[o] = fmaf(alpha, rv, bv);
+                    gw[o] = fmaf(alpha, rw, bw);
+                }
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) {
+            aborted = true;
+            break;
+        }
+        // level K-1 is no longer needed: refill its slot
+        if (tid == 0 && lp >= 1 && issued < np) {
+            fence_proxy_async_smem();
+            issue(issued);
+            ++issued;
+        }
+    }
+    if (aborted && tid == 0) {
+        report_error(err, DEV_TIMEOUT_TMA_WAIT);
+        for (int p = waited; p < issued; ++p)
+            if (!mbar_wait_bounded(&bars[p % S], (p / S) & 1, kDrainLimitNs)) break;
+    }
+}
+
+constexpr int kAdjTY = 4, kAdjS = 5;
+
+cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
+                               float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
+                               cudaStream_t s) {
+    using L = AdjLayout<kAdjTY, kAdjS>;
+    auto kern = adjoint_tma_kernel<kAdjTY, kAdjS>;
+    cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
+    if (e != cudaSuccess) return e;
+    AdjMaps m;
+    for (int f = 0; f < 6; ++f) m.m[f] = maps6[f];
+    dim3 grid((g.nx + kAdjTX - 1) / kAdjTX, (g.ny + kAdjTY - 1) / kAdjTY, nseg);
+    kern<<<grid, dim3(32, kAdjTY), L::SMEM, s>>>(m, gu, gv, gw, g, ox, nseg, cf, alpha, accumulate, add_lambda, err);
+    return cudaGetLastError();
+}
+
+int adjoint_tma_rows() { return kAdjTY; }
+
 cudaError_t launch_adjoint(const GridDev& g, const float* u, const float* v, const float* w, const float* lu,
                            const float* lv, const float* lw, float* gu, float* gv, float* gw, float alpha,
                            int accumulate, int add_lambda, int periodic, const CoefDev& cf, int num_sms,

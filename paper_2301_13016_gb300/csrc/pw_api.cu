@@ -518,11 +518,40 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
     if (gu == gv || gu == gw || gv == gw) return fail(PW_ERR_ARG, "outputs alias each other");
     if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return fail(PW_ERR_ARG, "alpha must be finite");
     CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int ox = 0;
+    const char* why = "";
+    bool ptrs_ok = true;
+    for (auto p : ins) ptrs_ok = ptrs_ok && aligned16(p);
+    if ((flags & PW_ADJ_PERIODIC) && h->kernel_kind != 1 && ptrs_ok && tma_layout_ok(h->grid, &ox, &why)) {
+        // TMA k-march adjoint: the sensitivities need periodic halos too
+        const GridDev g = to_dev(h->grid);
+        for (int q = 3; q < 6; ++q) {
+            cudaError_t e = launch_fill_halo(PW_F32, g, const_cast<void*>(ins[q]), h->num_sms, s);
+            if (e != cudaSuccess) return cuda_fail(e, "sensitivity halo fill");
+        }
+        CUtensorMap maps[6];
+        const int rows = adjoint_tma_rows();
+        for (int q = 0; q < 6; ++q) {
+            pw_status_t st = encode_map(h, ins[q], ox, 32, rows, &maps[q]);
+            if (st != PW_OK) return st;
+        }
+        const long long tiles = (long long)((g.nx + 127) / 128) * ((g.ny + rows - 1) / rows);
+        int nseg = 1;
+        while (tiles * nseg < 4LL * h->num_sms && g.nz / (nseg * 2) >= 8) nseg *= 2;
+        cudaError_t e = launch_adjoint_tma(g, ox, maps, (float*)gu, (float*)gv, (float*)gw, alpha,
+                                           (flags & PW_ADJ_ACCUMULATE) ? 1 : 0, (flags & PW_ADJ_ADD_LAMBDA) ? 1 : 0,
+                                           cf, nseg, h->d_err, s);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+        h->last_kernel = 2;
+        return PW_OK;
+    }
+    h->last_kernel = 1;
     cudaError_t e = launch_adjoint(to_dev(h->grid), (const float*)u, (const float*)v, (const float*)w,
                                    (const float*)lsu, (const float*)lsv, (const float*)lsw, (float*)gu, (float*)gv,
                                    (float*)gw, alpha, (flags & PW_ADJ_ACCUMULATE) ? 1 : 0,
                                    (flags & PW_ADJ_ADD_LAMBDA) ? 1 : 0, (flags & PW_ADJ_PERIODIC) ? 1 : 0, cf,
-                                   h->num_sms, reinterpret_cast<cudaStream_t>(stream));
+                                   h->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
     return PW_OK;
 }

@@ -220,14 +220,9 @@ struct TmaLayout {
     static_assert(TY % RPW == 0, "TY must be a multiple of the rows per warp");
 };
 
-// Build-time knobs of the k-march kernel (defaults are the measured best):
-// PW_TMA_UNROLL   1 = march in blocks of S levels with compile-time ring
-//                 slots, 0 = one level per loop trip;
-// PW_TMA_MAX_MINB cap on the resident CTAs per SM the register budget is
-//                 sized for.
-#ifndef PW_TMA_UNROLL
-#define PW_TMA_UNROLL 0
-#endif
+// Build-time knob of the k-march kernel: PW_TMA_MAX_MINB caps the resident
+// CTAs per SM the register budget is sized for (a cap of 3 made the 8-row
+// shapes spill; 2 does not).
 #ifndef PW_TMA_MAX_MINB
 #define PW_TMA_MAX_MINB 2
 #endif

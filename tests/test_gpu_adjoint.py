@@ -64,12 +64,15 @@ def test_adjoint_full_array_matches_oracle(shape, anelastic):
         assert torch.isnan(v[0]).all() and torch.isnan(v[-1]).all()
 
 
-@pytest.mark.parametrize("shape", [(64, 12, 8), (36, 7, 6)])
-def test_adjoint_periodic_matches_folded_oracle(shape):
+@pytest.mark.parametrize("shape", [(64, 12, 8), (36, 7, 6), (260, 9, 5), (128, 16, 20)])
+@pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
+def test_adjoint_periodic_matches_folded_oracle(shape, kernel):
     c, q, lam, g, h, dq, dl = _setup(*shape, periodic_q=True)
     out = [g.alloc(fill=NAN) for _ in range(3)]
+    h.set_kernel(kernel)
     h.adjoint(*dq, *dl, *out, alpha=1.0, flags=pwlib.PW_ADJ_PERIODIC)
     h.sync()
+    assert h.last_kernel == kernel
     # the oracle's adjoint sees the lambda entries at the scheme's outputs only
     lam_int = []
     for x in lam:
@@ -85,8 +88,10 @@ def test_adjoint_periodic_matches_folded_oracle(shape):
         assert torch.isnan(v[1:-1, 0]).all() and torch.isnan(v[1:-1, :, 0]).all()   # halo not written
 
 
-def test_adjoint_accumulate_and_add_lambda():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
+def test_adjoint_accumulate_and_add_lambda(kernel):
     c, q, lam, g, h, dq, dl = _setup(64, 10, 6, periodic_q=True)
+    h.set_kernel(kernel)
     base = [g.from_dense(_rand_dense(64, 10, 6, s)) for s in (7, 8, 9)]
     plain = [g.alloc() for _ in range(3)]
     h.adjoint(*dq, *dl, *plain, alpha=0.5, flags=pwlib.PW_ADJ_PERIODIC)
