@@ -119,14 +119,18 @@ pw_status_t pw_destroy(pw_handle_t h);
 pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
 
 /*
- * Launch shape of the TMA k-march kernel: lanes_x = lanes per row (32: tiles
- * 128 columns wide; 16: 64 columns, for narrow grids), ty = rows per CTA,
- * stages = planes buffered per CTA, nseg = CTAs along z (0 = chosen from the
- * grid and SM count).  Any argument 0 keeps the automatic choice (32, 4, 4).
- * Instantiated shapes (lanes_x, ty, stages): (32,4,4) (32,8,3) (32,8,4)
- * (32,8,6) (32,16,3) (16,4,4) (16,8,4); others give PW_ERR_UNSUPPORTED.
+ * Launch shape of the TMA k-march kernel: lanes_x = lanes per row, cells =
+ * consecutive cells per thread along x (tile width lanes_x * cells columns),
+ * ty = rows per CTA, stages = planes buffered per CTA, nseg = CTAs along z
+ * (0 = chosen from the grid and SM count).  Any argument 0 keeps the
+ * automatic choice: (32, 4, 4, 4) for FP32, (16, 8, 4, 4) for 16-bit storage
+ * when nx is a multiple of 8.  Instantiated (lanes_x, ty, stages, cells):
+ * (32,4,4,4) (32,8,3,4) (32,8,4,4) (32,8,6,4) (32,16,3,4) (16,4,4,4)
+ * (16,8,4,4), and for 16-bit storage also (16,4,4,8) (16,8,4,8); others, and
+ * cells = 8 with nx not a multiple of 8, give PW_ERR_UNSUPPORTED.
  */
-pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t ty, int32_t stages, int32_t nseg);
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
+                              int32_t nseg);
 
 /*
  * Source terms su, sv, sw of the PW scheme (Sec. 2.2; arithmetic shape

@@ -18,8 +18,9 @@ import torch
 
 BATCH_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=4, ctas_per_sm=c)
                     for lx, ty in ((32, 4), (32, 8), (16, 4), (16, 8)) for c in (0, 2)]
-GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns)
-                   for lx, ty, st in ((32, 4, 4), (32, 8, 4), (32, 8, 6), (16, 4, 4), (16, 8, 4))
+GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns, cells=nc)
+                   for lx, ty, st, nc in ((32, 4, 4, 4), (32, 8, 4, 4), (32, 8, 6, 4), (16, 4, 4, 4), (16, 8, 4, 4),
+                                          (16, 4, 4, 8), (16, 8, 4, 8))
                    for ns in (0, 1, 2, 4)]
 
 
@@ -160,15 +161,18 @@ def main(argv=None):
     res = {}
     seen = set()
     for cand in GRID_CANDIDATES:
-        key = (cand["lanes_x"], cand["ty"], cand["stages"])
+        key = (cand["lanes_x"], cand["ty"], cand["stages"], cand["cells"])
         if key in seen:
             continue
         seen.add(key)
-        h.set_tma_config(cand["ty"], cand["stages"], 0, lanes_x=cand["lanes_x"])
+        try:
+            h.set_tma_config(cand["ty"], cand["stages"], 0, lanes_x=cand["lanes_x"], cells=cand["cells"])
+        except RuntimeError:
+            continue
         ms_t = _time(lambda: h.tendencies(*dev, *outs, scale=sc, stream=stream), 3, a.reps, stream)
         ms_s = _time(lambda: h.step(*dev, *tmp, 0.0, 2, scale=sc[:3], stream=stream), 2, a.reps, stream) / 2
         h.sync(stream)
-        res[f"lanes{key[0]}_ty{key[1]}_s{key[2]}"] = {"tend_gcells": g.cells / ms_t / 1e6,
+        res[f"lanes{key[0]}_ty{key[1]}_s{key[2]}_c{key[3]}"] = {"tend_gcells": g.cells / ms_t / 1e6,
                                                       "step_gcells": g.cells / ms_s / 1e6}
     print(json.dumps({"grid": [a.nx, a.ny, a.nz], "dtype": a.dtype, "tag": a.tag, "device": _device_key(),
                       "shapes": res}), flush=True)

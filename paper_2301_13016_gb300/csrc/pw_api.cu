@@ -58,7 +58,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 struct MapCacheEntry {
     const void* ptr = nullptr;
-    int ty = 0, lx = 0;
+    int ty = 0, lx = 0, nc = 0;
     CUtensorMap map;
 };
 
@@ -79,8 +79,12 @@ struct pw_handle_s {
     TmaConfig tma_auto{0, 0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
-    // pw_tendencies_host staging
+    // pw_tendencies_host staging and its copy / compute pipeline
     void* d_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};   // copy in, compute, copy out
+    static constexpr int kMaxChunks = 16;
+    cudaEvent_t ev_in[kMaxChunks] = {}, ev_comp[kMaxChunks] = {};
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
     // validation scratch: 4*(nblocks+1) doubles + wk (nz+2 doubles)
     double* d_scratch = nullptr;
     int nblocks = 0;
@@ -140,24 +144,27 @@ bool pw::tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
 
 bool pw::aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out) {
+static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
+                              int nc = 4) {
     for (auto& c : h->maps)
-        if (c.ptr == ptr && c.ty == ty && c.lx == lx) {
+        if (c.ptr == ptr && c.ty == ty && c.lx == lx && c.nc == nc) {
             *out = c.map;
             return PW_OK;
         }
     MapCacheEntry& e = h->maps[h->map_next];
     h->map_next = (h->map_next + 1) % (int)(sizeof(h->maps) / sizeof(h->maps[0]));
-    pw_status_t st = encode_tensor_map(h->grid, ptr, ox, lx, ty, out);
+    pw_status_t st = encode_tensor_map(h->grid, ptr, ox, lx, ty, out, nc);
     if (st != PW_OK) return st;
     e.ptr = ptr;
     e.ty = ty;
     e.lx = lx;
+    e.nc = nc;
     e.map = *out;
     return PW_OK;
 }
 
-pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out) {
+pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
+                                  int nc) {
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const size_t es = dtype_size(g.dtype);
@@ -167,7 +174,7 @@ pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, i
     cuuint64_t dims[3] = {(cuuint64_t)(ox + g.nx + g.halo + 1), (cuuint64_t)(g.ny + 2 * g.halo),
                           (cuuint64_t)(g.nz + 2)};
     cuuint64_t strides[2] = {(cuuint64_t)(g.pitch_j * es), (cuuint64_t)(g.pitch_k * es)};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype, lx), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype, lx, nc), (cuuint32_t)(ty + 2), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(out, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -182,14 +189,17 @@ pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, i
 static TmaConfig choose_tma(pw_handle_t h) {
     if (h->tma_auto.ty) return h->tma_auto;
     TmaConfig c;
-    c.lx = h->tma_user.lx ? h->tma_user.lx : 32;
+    // 16-bit storage with nx a multiple of 8: 8 cells per thread, 16 lanes per row
+    const bool wide = dtype_size(h->grid.dtype) == 2 && h->grid.nx % 8 == 0;
+    c.lx = h->tma_user.lx ? h->tma_user.lx : (wide ? 16 : 32);
+    c.nc = h->tma_user.nc ? h->tma_user.nc : (wide ? 8 : 4);
     c.ty = h->tma_user.ty ? h->tma_user.ty : 4;
     c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
     if (h->tma_user.nseg) {
         c.nseg = h->tma_user.nseg;
     } else {
         const long long tiles =
-            (long long)((h->grid.nx + 4 * c.lx - 1) / (4 * c.lx)) * ((h->grid.ny + c.ty - 1) / c.ty);
+            (long long)((h->grid.nx + c.nc * c.lx - 1) / (c.nc * c.lx)) * ((h->grid.ny + c.ty - 1) / c.ty);
         int bps = tma_blocks_per_sm(h->grid.dtype, c);
         if (bps < 1) bps = 1;
         const long long slots = (long long)h->num_sms * bps;
@@ -310,6 +320,14 @@ pw_status_t pw_create(const pw_grid_t* grid, const pw_coeffs_t* coeffs, pw_handl
 
 pw_status_t pw_destroy(pw_handle_t h) {
     if (!h) return PW_OK;
+    for (auto& st : h->hs)
+        if (st) cudaStreamDestroy(st);
+    for (int c = 0; c < pw_handle_s::kMaxChunks; ++c) {
+        if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+        if (h->ev_comp[c]) cudaEventDestroy(h->ev_comp[c]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_end) cudaEventDestroy(h->ev_end);
     cudaFree(h->d_tz);
     cudaFree(h->d_err);
     for (auto& p : h->d_stage) cudaFree(p);
@@ -325,14 +343,18 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind) {
     return PW_OK;
 }
 
-pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t ty, int32_t stages, int32_t nseg) {
+pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
+                              int32_t nseg) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
     TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
+    c.nc = cells ? cells : 4;
     if (!tma_config_supported(h->grid.dtype, c))
-        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for lanes_x=%d ty=%d stages=%d", c.lx, c.ty,
-                    c.stages);
+        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for lanes_x=%d cells=%d ty=%d stages=%d (dtype %d)",
+                    c.lx, c.nc, c.ty, c.stages, (int)h->grid.dtype);
+    if (h->grid.nx % c.nc) return fail(PW_ERR_UNSUPPORTED, "cells=%d needs nx to be a multiple of %d", c.nc, c.nc);
     h->tma_user = TmaConfig{lanes_x, ty, stages, nseg};
+    h->tma_user.nc = cells;
     h->tma_auto = TmaConfig{0, 0, 0, 0};
     for (auto& m : h->maps) m.ptr = nullptr;
     return PW_OK;
@@ -375,7 +397,7 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         TmaConfig c = choose_tma(h);
         CUtensorMap maps[3];
         for (int q = 0; q < 3; ++q) {
-            pw_status_t st = encode_map(h, ins[q], ox, c.lx, c.ty, &maps[q]);
+            pw_status_t st = encode_map(h, ins[q], ox, c.lx, c.ty, &maps[q], c.nc);
             if (st != PW_OK) return st;
         }
         cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, scaled, cf, h->d_err, c, s);
@@ -403,24 +425,104 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
             e = cudaMemset(p, 0, bytes);
             if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging clear");
         }
-    // levels 1..nz (the z-halo planes are never read), full padded rows
-    const size_t lo = (size_t)(g.origin + g.pitch_k + (long long)(1 - g.halo) * g.pitch_j + 1 - g.halo);
-    const size_t hi = (size_t)(g.origin + (long long)g.nz * g.pitch_k + (long long)(g.ny + g.halo) * g.pitch_j +
-                               g.nx + g.halo + 1);
-    const size_t off = lo * es, len = (hi - lo) * es;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
     const void* hin[3] = {u, v, w};
     void* hout[3] = {su, sv, sw};
-    for (int q = 0; q < 3; ++q)
-        PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len, cudaMemcpyHostToDevice, s),
-                "pw_tendencies_host input copy");
-    pw_status_t st = pw_tendencies(h, h->d_stage[0], h->d_stage[1], h->d_stage[2], h->d_stage[3], h->d_stage[4],
-                                   h->d_stage[5], scale, stream);
-    if (st != PW_OK) return st;
-    for (int q = 0; q < 3; ++q)
-        PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len, cudaMemcpyDeviceToHost, s),
-                "pw_tendencies_host output copy");
-    PW_CUDA(cudaStreamSynchronize(s), "pw_tendencies_host synchronize");
+    // contiguous element span of levels a..b (full padded planes)
+    auto span = [&](int a, int b, size_t* off, size_t* len) {
+        const long long lo = g.origin + (long long)a * g.pitch_k + (long long)(1 - g.halo) * g.pitch_j + 1 - g.halo;
+        const long long hi = g.origin + (long long)b * g.pitch_k + (long long)(g.ny + g.halo) * g.pitch_j + g.nx +
+                             g.halo + 1;
+        *off = (size_t)lo * es;
+        *len = (size_t)(hi - lo) * es;
+    };
+
+    int ox = 0;
+    const char* why = "";
+    bool ptrs_ok = true;
+    for (auto p : h->d_stage) ptrs_ok = ptrs_ok && aligned16(p);
+    const bool pipelined = h->kernel_kind != 1 && ptrs_ok && tma_layout_ok(g, &ox, &why) && g.nz >= 8;
+    if (!pipelined) {   // one copy in, one launch, one copy out
+        size_t off, len;
+        span(1, g.nz, &off, &len);
+        for (int q = 0; q < 3; ++q)
+            PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len, cudaMemcpyHostToDevice,
+                                    us),
+                    "pw_tendencies_host input copy");
+        pw_status_t st = pw_tendencies(h, h->d_stage[0], h->d_stage[1], h->d_stage[2], h->d_stage[3], h->d_stage[4],
+                                       h->d_stage[5], scale, stream);
+        if (st != PW_OK) return st;
+        for (int q = 0; q < 3; ++q)
+            PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len,
+                                    cudaMemcpyDeviceToHost, us),
+                    "pw_tendencies_host output copy");
+        PW_CUDA(cudaStreamSynchronize(us), "pw_tendencies_host synchronize");
+        return PW_OK;
+    }
+
+    // Pipelined over k chunks: chunk c's input planes travel on stream 0
+    // while chunk c-1 is computed on stream 1 and chunk c-2's outputs travel
+    // back on stream 2 (the two copy directions and the kernels overlap).
+    for (auto& st : h->hs)
+        if (!st) PW_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "pipeline stream");
+    for (int c = 0; c < pw_handle_s::kMaxChunks; ++c) {
+        if (!h->ev_in[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming), "pipeline event");
+        if (!h->ev_comp[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_comp[c], cudaEventDisableTiming), "pipeline event");
+    }
+    if (!h->ev_start) PW_CUDA(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming), "pipeline event");
+    if (!h->ev_end) PW_CUDA(cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming), "pipeline event");
+    const int C = std::min(pw_handle_s::kMaxChunks, std::max(2, g.nz / 4));
+    Scales sc;
+    bool scaled;
+    if (scale)
+        for (int q = 0; q < 6; ++q)
+            if (!(scale[q] > 0.f) || !(scale[q] < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
+    make_scales(scale, &sc, &scaled);
+    TmaConfig cfg = choose_tma(h);
+    cfg.nseg = C;
+    cfg.seg_count = 1;
+    CUtensorMap maps[3];
+    for (int q = 0; q < 3; ++q) {
+        pw_status_t st = encode_map(h, h->d_stage[q], ox, cfg.lx, cfg.ty, &maps[q], cfg.nc);
+        if (st != PW_OK) return st;
+    }
+    const GridDev gd = to_dev(g);
+    CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    PW_CUDA(cudaEventRecord(h->ev_start, us), "pipeline event");
+    for (auto st : h->hs) PW_CUDA(cudaStreamWaitEvent(st, h->ev_start, 0), "pipeline wait");
+    int copied = 0;   // input levels 1..copied are on their way
+    for (int c = 0; c < C; ++c) {
+        const int kb = 1 + (int)(((long long)c * g.nz) / C);
+        const int ke = (int)(((long long)(c + 1) * g.nz) / C);
+        const int need = std::min(ke + 1, g.nz);
+        if (need > copied) {
+            size_t off, len;
+            span(copied + 1, need, &off, &len);
+            for (int q = 0; q < 3; ++q)
+                PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len,
+                                        cudaMemcpyHostToDevice, h->hs[0]),
+                        "pw_tendencies_host input copy");
+            copied = need;
+        }
+        PW_CUDA(cudaEventRecord(h->ev_in[c], h->hs[0]), "pipeline event");
+        PW_CUDA(cudaStreamWaitEvent(h->hs[1], h->ev_in[c], 0), "pipeline wait");
+        cfg.seg0 = c;
+        cudaError_t e = launch_tend_tma(g.dtype, gd, ox, maps, h->d_stage[3], h->d_stage[4], h->d_stage[5], sc, scaled,
+                                        cf, h->d_err, cfg, h->hs[1]);
+        if (e != cudaSuccess) return cuda_fail(e, "TMA tendency kernel launch");
+        PW_CUDA(cudaEventRecord(h->ev_comp[c], h->hs[1]), "pipeline event");
+        PW_CUDA(cudaStreamWaitEvent(h->hs[2], h->ev_comp[c], 0), "pipeline wait");
+        size_t off, len;
+        span(kb, ke, &off, &len);
+        for (int q = 0; q < 3; ++q)
+            PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len,
+                                    cudaMemcpyDeviceToHost, h->hs[2]),
+                    "pw_tendencies_host output copy");
+    }
+    h->last_kernel = 2;
+    PW_CUDA(cudaEventRecord(h->ev_end, h->hs[2]), "pipeline event");
+    PW_CUDA(cudaStreamWaitEvent(us, h->ev_end, 0), "pipeline wait");
+    PW_CUDA(cudaStreamSynchronize(h->hs[2]), "pw_tendencies_host synchronize");
     return PW_OK;
 }
 
@@ -471,7 +573,7 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
         if (use_tma) {
             CUtensorMap maps[3];
             for (int q = 0; q < 3; ++q) {
-                pw_status_t st = encode_map(h, src[q], ox, c.lx, c.ty, &maps[q]);
+                pw_status_t st = encode_map(h, src[q], ox, c.lx, c.ty, &maps[q], c.nc);
                 if (st != PW_OK) return st;
             }
             e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);

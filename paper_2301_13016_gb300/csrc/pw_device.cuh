@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pw {
 
 // ---------------------------------------------------------------------------
@@ -64,6 +66,67 @@ __device__ __forceinline__ void store4(__half* p, const float (&v)[4]) {
     t.x = *reinterpret_cast<uint32_t*>(&a);
     t.y = *reinterpret_cast<uint32_t*>(&b);
     *reinterpret_cast<uint2*>(p) = t;
+}
+
+// N consecutive elements (N = 4 or 8) <-> float[N]; p aligned to N*sizeof(T)
+// (8 16-bit elements are one 16-byte access).
+template <int N, typename T>
+__device__ __forceinline__ void loadv(const T* p, float (&o)[N]) {
+    if constexpr (N == 4) {
+        load4(p, o);
+    } else {
+        static_assert(N == 8, "N must be 4 or 8");
+        if constexpr (sizeof(T) == 4) {
+            float a[4], b[4];
+            load4(p, a);
+            load4(p + 4, b);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                o[q] = a[q];
+                o[4 + q] = b[q];
+            }
+        } else {
+            const uint4 t = *reinterpret_cast<const uint4*>(p);
+            const uint32_t w4[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 f;
+                if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value)
+                    f = __half22float2(*reinterpret_cast<const __half2*>(&w4[q]));
+                else
+                    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[q]));
+                o[2 * q] = f.x;
+                o[2 * q + 1] = f.y;
+            }
+        }
+    }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void storev(T* p, const float (&v)[N]) {
+    if constexpr (N == 4) {
+        store4(p, v);
+    } else {
+        static_assert(N == 8, "N must be 4 or 8");
+        if constexpr (sizeof(T) == 4) {
+            const float a[4] = {v[0], v[1], v[2], v[3]}, b[4] = {v[4], v[5], v[6], v[7]};
+            store4(p, a);
+            store4(p + 4, b);
+        } else {
+            uint32_t w4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if constexpr (std::is_same<T, __half>::value) {
+                    __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+                    w4[q] = *reinterpret_cast<uint32_t*>(&h);
+                } else {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    w4[q] = *reinterpret_cast<uint32_t*>(&h);
+                }
+            }
+            *reinterpret_cast<uint4*>(p) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

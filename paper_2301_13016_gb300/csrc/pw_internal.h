@@ -35,7 +35,10 @@ struct TmaConfig {
     int lx;      // lanes per row: 32 (tile 128 columns wide) or 16 (64 columns)
     int ty;      // interior rows per CTA
     int stages;  // planes resident or in flight per CTA
-    int nseg;    // k segments (CTAs along z)
+    int nseg;    // k segments the levels are split into
+    int nc = 4;         // cells per thread along x (8: 16-bit storage only)
+    int seg0 = 0;       // first segment to launch
+    int seg_count = 0;  // segments to launch (0 = all nseg)
 };
 
 size_t dtype_size(pw_dtype_t t);
@@ -45,7 +48,7 @@ cudaError_t launch_tend_generic(pw_dtype_t dt, const GridDev& g, const void* u, 
                                 const CoefDev& cf, int num_sms, cudaStream_t s);
 
 // Box width (elements along x) of one TMA load for this dtype and tile width.
-int tma_box_width(pw_dtype_t dt, int lx);
+int tma_box_width(pw_dtype_t dt, int lx, int nc = 4);
 // True if an instantiation exists for (dtype, ty, stages).
 bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c);
 size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c);
@@ -102,6 +105,7 @@ bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
 pw_status_t validate_grid(const pw_grid_t* g);
 bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why);
 bool aligned16(const void* p);
-pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out);
+pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
+                              int nc = 4);
 
 }  // namespace pw

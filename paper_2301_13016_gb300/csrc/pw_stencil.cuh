@@ -28,12 +28,13 @@ struct Epilogue<T, MODE_TEND> {
         o1[o] = Store<T>::from_f(b);
         o2[o] = Store<T>::from_f(c);
     }
-    static __device__ __forceinline__ void store4v(T* o0, T* o1, T* o2, long long o, const float (&a)[4],
-                                                   const float (&b)[4], const float (&c)[4], const GridDev&, int,
-                                                   int) {
-        store4(o0 + o, a);
-        store4(o1 + o, b);
-        store4(o2 + o, c);
+    template <int N>
+    static __device__ __forceinline__ void storevec(T* o0, T* o1, T* o2, long long o, const float (&a)[N],
+                                                    const float (&b)[N], const float (&c)[N], const GridDev&, int,
+                                                    int) {
+        storev<N>(o0 + o, a);
+        storev<N>(o1 + o, b);
+        storev<N>(o2 + o, c);
     }
 };
 
@@ -67,22 +68,18 @@ struct Epilogue<T, MODE_STEP> {
             if (dxm) put(o + dym + dxm);
         }
     }
-    // a vector of 4 cells (j, i0..i0+3), i0 = 1 mod 4, nx = 0 mod 4
-    static __device__ __forceinline__ void store4v(T* o0, T* o1, T* o2, long long o, const float (&a)[4],
-                                                   const float (&b)[4], const float (&c)[4], const GridDev& g, int j,
-                                                   int i0) {
-        store4(o0 + o, a);
-        store4(o1 + o, b);
-        store4(o2 + o, c);
+    // a vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
+    template <int N>
+    static __device__ __forceinline__ void storevec(T* o0, T* o1, T* o2, long long o, const float (&a)[N],
+                                                    const float (&b)[N], const float (&c)[N], const GridDev& g, int j,
+                                                    int i0) {
+        storev<N>(o0 + o, a);
+        storev<N>(o1 + o, b);
+        storev<N>(o2 + o, c);
         if (g.halo != 1) return;
-        const bool west = (i0 == 1), east = (i0 + 3 == g.nx);
+        const bool west = (i0 == 1), east = (i0 + N - 1 == g.nx);
         const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
         const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
-        auto row = [&](long long p) {   // the row image plus its corner images
-            store4(o0 + p, a);
-            store4(o1 + p, b);
-            store4(o2 + p, c);
-        };
         auto cell = [&](long long p, int q) {
             o0[p] = Store<T>::from_f(a[q]);
             o1[p] = Store<T>::from_f(b[q]);
@@ -93,9 +90,13 @@ struct Epilogue<T, MODE_STEP> {
         for (int s = 0; s < 3; ++s) {
             if (s > 0 && shifts[s] == 0) continue;
             const long long p = o + shifts[s];
-            if (s > 0) row(p);
-            if (west) cell(p + g.nx, 0);            // cell i = 1 -> i = nx+1
-            if (east) cell(p + 3 - g.nx, 3);        // cell i = nx (offset +3) -> i = 0
+            if (s > 0) {   // the row image
+                storev<N>(o0 + p, a);
+                storev<N>(o1 + p, b);
+                storev<N>(o2 + p, c);
+            }
+            if (west) cell(p + g.nx, 0);                   // cell i = 1 -> i = nx+1
+            if (east) cell(p + (N - 1) - g.nx, N - 1);     // cell i = nx -> i = 0
         }
     }
 };
@@ -201,9 +202,9 @@ static cudaError_t launch_generic_mode(const GridDev& g, const void* u, const vo
 // Ring bookkeeping is global to the CTA: the n-th plane a CTA ever issues
 // goes to slot n % S and completes phase (n / S) & 1 of that slot's mbarrier,
 // so a persistent CTA can march tile after tile without re-initialising.
-template <typename T, int LX, int TY, int S>
+template <typename T, int LX, int TY, int S, int NC = 4>
 struct TmaLayout {
-    static constexpr int TX = 4 * LX;
+    static constexpr int TX = NC * LX;
     static constexpr int RPW = 32 / LX;                // rows per warp
     static constexpr int WARPS = TY / RPW;
     static constexpr int THREADS = 32 * WARPS;
@@ -217,6 +218,8 @@ struct TmaLayout {
     static constexpr uint32_t TX_BYTES = 3u * FIELD_RAW * (uint32_t)sizeof(T);
     static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16;
     static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
+    static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
+    static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
     static_assert(TY % RPW == 0, "TY must be a multiple of the rows per warp");
 };
 
@@ -229,9 +232,9 @@ struct TmaLayout {
 
 // Resident CTAs per SM the register budget is sized for: what shared memory
 // and the thread limit allow, at most PW_TMA_MAX_MINB.
-template <typename T, int LX, int TY, int S>
+template <typename T, int LX, int TY, int S, int NC = 4>
 constexpr int tma_min_blocks() {
-    using L = TmaLayout<T, LX, TY, S>;
+    using L = TmaLayout<T, LX, TY, S, NC>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
     constexpr int m = by_smem < by_threads ? by_smem : by_threads;
@@ -240,9 +243,9 @@ constexpr int tma_min_blocks() {
 
 // Shared memory of a k-march CTA: the plane ring, one mbarrier per slot, and
 // the abort flag / work-item word.
-template <typename T, int LX, int TY, int S>
+template <typename T, int LX, int TY, int S, int NC = 4>
 struct MarchSmem {
-    using L = TmaLayout<T, LX, TY, S>;
+    using L = TmaLayout<T, LX, TY, S, NC>;
     T* stages;
     uint64_t* bars;
     volatile int* flag;   // flag[0]: abort, flag[1]: work item broadcast
@@ -266,14 +269,14 @@ struct MarchSmem {
 // `ring` counts the planes this CTA issued before; it is advanced by the
 // planes of this tile.  Returns false if a wait timed out (the error is
 // recorded and the copies in flight are drained).
-template <typename T, int LX, int TY, int S, bool SCALED, int MODE>
-__device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, const CUtensorMap* tm_u,
+template <typename T, int LX, int TY, int S, bool SCALED, int MODE, int NC = 4>
+__device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC>& sm, const CUtensorMap* tm_u,
                                            const CUtensorMap* tm_v, const CUtensorMap* tm_w, T* __restrict__ o0,
                                            T* __restrict__ o1, T* __restrict__ o2, const GridDev& g, const int ox,
                                            const Scales& sc, const CoefDev& cf, const float dt, const int bx,
                                            const int by, const int kb, const int ke, uint32_t& ring,
                                            int* __restrict__ err) {
-    using L = TmaLayout<T, LX, TY, S>;
+    using L = TmaLayout<T, LX, TY, S, NC>;
     constexpr int BW = L::BW;
     constexpr int PADX = L::PADX;
     constexpr int FU = 0, FV = L::FIELD, FW = 2 * L::FIELD;
@@ -316,12 +319,12 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
     }
 
     const int r = row + 1;
-    const int c0 = 4 * xl + PADX;
+    const int c0 = NC * xl + PADX;
     // tile-edge neighbour column: the row's first lane needs x = -1, its last
     // lane x = TX; the other lanes read the last lane's address (a broadcast)
     const int ce = (xl == 0) ? PADX - 1 : L::TX + PADX;
     const int j = TY * by + 1 + row;
-    const int i0 = 1 + L::TX * bx + 4 * xl;
+    const int i0 = 1 + L::TX * bx + NC * xl;
     const bool valid = (j <= g.ny) && (i0 <= g.nx);
     const long long row_off = g.origin + (long long)j * g.pj + i0;
     const float tcx = cf.tcx, tcy = cf.tcy;
@@ -329,33 +332,33 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
     const unsigned FULL = 0xffffffffu;
     const float su_in = sc.in[0], sv_in = sc.in[1], sw_in = sc.in[2];
 
-    auto ld = [&](const T* p, float (&o)[4], float s) {
-        load4(p, o);
+    auto ld = [&](const T* p, float (&o)[NC], float s) {
+        loadv<NC>(p, o);
         if (SCALED) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] *= s;
+            for (int q = 0; q < NC; ++q) o[q] *= s;
         }
     };
     auto ld1 = [&](const T* p, float s) {
         float x = Store<T>::to_f(*p);
         return SCALED ? x * s : x;
     };
-    // x-neighbours of a row vector: value at x = -1 (m) and x = 4 (p)
-    auto nbr_m = [&](const float (&x)[4], float edge) {
-        float m = __shfl_up_sync(FULL, x[3], 1, LX);
+    // x-neighbours of a row vector: value at x = -1 (m) and x = NC (p)
+    auto nbr_m = [&](const float (&x)[NC], float edge) {
+        float m = __shfl_up_sync(FULL, x[NC - 1], 1, LX);
         return xl == 0 ? edge : m;
     };
-    auto nbr_p = [&](const float (&x)[4], float edge) {
+    auto nbr_p = [&](const float (&x)[NC], float edge) {
         float p = __shfl_down_sync(FULL, x[0], 1, LX);
         return xl == LX - 1 ? edge : p;
     };
 
     // rows of level kk carried from the previous step (loaded there as level kk+1)
-    float u0[4], v0[4], vs[4], w0[4];
+    float u0[NC], v0[NC], vs[NC], w0[NC];
     // level kk-1 at the cell, and the lower vertical pair sums of level kk
-    float ud[4], vd[4], wd[4], pzu[4], pzv[4], pzw[4];
+    float ud[NC], vd[NC], wd[NC], pzu[NC], pzv[NC], pzw[NC];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NC; ++c) {
         ud[c] = vd[c] = wd[c] = pzu[c] = pzv[c] = pzw[c] = 0.f;
         u0[c] = v0[c] = vs[c] = w0[c] = 0.f;
     }
@@ -379,14 +382,19 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
                 ld(P + FV + (r - 1) * BW + c0, vs, sv_in);
                 ld(P + FW + r * BW + c0, w0, sw_in);
             }
-            float wn[4];
+            float wn[NC];
             ld(P + FW + (r + 1) * BW + c0, wn, sw_in);
             const float ew = ld1(P + FW + r * BW + ce, sw_in);
-            const float w0m = nbr_m(w0, ew), w0p = nbr_p(w0, ew);
-            const float W[6] = {w0m, w0[0], w0[1], w0[2], w0[3], w0p};   // x = -1..4
+            float W[NC + 2];   // x = -1..NC
+            W[0] = nbr_m(w0, ew);
+            W[NC + 1] = nbr_p(w0, ew);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) W[c + 1] = w0[c];
 
             // level kk+1 rows (upper terms; carried into the next step)
-            float uu[4] = {0, 0, 0, 0}, vu[4] = {0, 0, 0, 0}, vus[4] = {0, 0, 0, 0}, wu[4] = {0, 0, 0, 0};
+            float uu[NC], vu[NC], vus[NC], wu[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) uu[c] = vu[c] = vus[c] = wu[c] = 0.f;
             float euu = 0.f;
             if (have_up) {
                 const T* Q = stages + slot(lp + 1) * L::STAGE;
@@ -397,18 +405,20 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
                 euu = ld1(Q + FU + r * BW + ce, su_in);
             }
             // upper vertical pair sums of level kk = lower ones of level kk+1
-            float pzu_n[4], pzv_n[4], pzw_n[4];
+            float pzu_n[NC], pzv_n[NC], pzw_n[NC];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < NC; ++c) {
                 pzu_n[c] = W[c + 1] + W[c + 2];   // w(k,i) + w(k,i+1)
                 pzv_n[c] = w0[c] + wn[c];         // w(k,j) + w(k,j+1)
                 pzw_n[c] = w0[c] + wu[c];         // w(k) + w(k+1)
             }
 
             const bool compute = (kk >= kb) && (kk >= 2);
-            float ru[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, rw[4] = {0, 0, 0, 0};
+            float ru[NC], rv[NC], rw[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ru[c] = rv[c] = rw[c] = 0.f;
             if (compute) {
-                float us[4], un[4], vn[4], ws[4];
+                float us[NC], un[NC], vn[NC], ws[NC];
                 ld(P + FU + (r - 1) * BW + c0, us, su_in);
                 ld(P + FU + (r + 1) * BW + c0, un, su_in);
                 ld(P + FV + (r + 1) * BW + c0, vn, sv_in);
@@ -417,29 +427,42 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
                 const float ev = ld1(P + FV + r * BW + ce, sv_in);
                 const float eun = ld1(P + FU + (r + 1) * BW + ce, su_in);
                 const float evs = ld1(P + FV + (r - 1) * BW + ce, sv_in);
-                const float U[6] = {nbr_m(u0, eu), u0[0], u0[1], u0[2], u0[3], nbr_p(u0, eu)};
-                const float V[6] = {nbr_m(v0, ev), v0[0], v0[1], v0[2], v0[3], nbr_p(v0, ev)};
-                const float UN[5] = {nbr_m(un, eun), un[0], un[1], un[2], un[3]};   // x = -1..3
-                const float VS[5] = {vs[0], vs[1], vs[2], vs[3], nbr_p(vs, evs)};   // x = 0..4
-                const float UU[5] = {nbr_m(uu, euu), uu[0], uu[1], uu[2], uu[3]};   // x = -1..3
+                float U[NC + 2], V[NC + 2];   // x = -1..NC
+                float UN[NC + 1], UU[NC + 1];  // x = -1..NC-1
+                float VS[NC + 1];              // x = 0..NC
+                U[0] = nbr_m(u0, eu);
+                U[NC + 1] = nbr_p(u0, eu);
+                V[0] = nbr_m(v0, ev);
+                V[NC + 1] = nbr_p(v0, ev);
+                UN[0] = nbr_m(un, eun);
+                UU[0] = nbr_m(uu, euu);
+                VS[NC] = nbr_p(vs, evs);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    U[c + 1] = u0[c];
+                    V[c + 1] = v0[c];
+                    UN[c + 1] = un[c];
+                    UU[c + 1] = uu[c];
+                    VS[c] = vs[c];
+                }
 
                 // pair sums along x shared by neighbouring cells: index c is the
                 // pair (x = c-1, c)
-                float pxu[5], qx[5], rx[5], pxv[4], pys[4];
+                float pxu[NC + 1], qx[NC + 1], rx[NC + 1], pxv[NC], pys[NC];
 #pragma unroll
-                for (int c = 0; c < 5; ++c) {
+                for (int c = 0; c < NC + 1; ++c) {
                     pxu[c] = U[c] + U[c + 1];     // u(i-1) + u(i)
                     qx[c] = U[c] + UN[c];         // u(j,i-1) + u(j+1,i-1)
                     rx[c] = U[c] + UU[c];         // u(k,i-1) + u(k+1,i-1)
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     pxv[c] = V[c + 1] + V[c + 2];  // v(j,i) + v(j,i+1)
                     pys[c] = VS[c] + VS[c + 1];    // v(j-1,i) + v(j-1,i+1)
                 }
                 const float tz1 = __ldg(cf.tz + kk);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     // su
                     float x = tcx * fmaf(-U[c + 2], pxu[c + 1], U[c] * pxu[c]);
                     x = fmaf(tcy, fmaf(-un[c], pxv[c], us[c] * pys[c]), x);
@@ -454,7 +477,7 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
                     const float td1 = __ldg(cf.tz + 2 * nzp2 + kk);
                     const float td2 = __ldg(cf.tz + 3 * nzp2 + kk);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
+                    for (int c = 0; c < NC; ++c) {
                         ru[c] = fmaf(-tz2, uu[c] * pzu_n[c], ru[c]);
                         rv[c] = fmaf(-tz2, vu[c] * pzv_n[c], rv[c]);
                         float z = tcx * fmaf(-W[c + 2], rx[c + 1], W[c] * rx[c]);
@@ -466,9 +489,9 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
             }
 
             if (kk >= kb && valid) {
-                float a[4], b[4], d[4];
+                float a[NC], b[NC], d[NC];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     if (MODE == MODE_STEP) {   // at kk = 1 the source terms are 0
                         a[c] = fmaf(dt, ru[c], u0[c]);
                         b[c] = fmaf(dt, rv[c], v0[c]);
@@ -484,12 +507,13 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
                         d[c] *= sc.out[2];
                     }
                 }
-                Epilogue<T, MODE>::store4v(o0, o1, o2, row_off + (long long)kk * g.pk, a, b, d, g, j, i0);
+                Epilogue<T, MODE>::template storevec<NC>(o0, o1, o2, row_off + (long long)kk * g.pk, a, b, d, g, j,
+                                                         i0);
             }
 
             // roll: level kk becomes level k-1, level kk+1 becomes level kk
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < NC; ++c) {
                 ud[c] = u0[c];
                 vd[c] = v0[c];
                 wd[c] = w0[c];
@@ -526,52 +550,63 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S>& sm, co
 }
 
 // One grid, one tile per CTA: blockIdx = (tile column, tile row, k segment).
-template <typename T, int LX, int TY, int S, bool SCALED, int MODE>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (tma_min_blocks<T, LX, TY, S>()))
+template <typename T, int LX, int TY, int S, bool SCALED, int MODE, int NC>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC>::THREADS, (tma_min_blocks<T, LX, TY, S, NC>()))
     tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
                const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
-               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const Scales sc,
+               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const int seg0, const Scales sc,
                const CoefDev cf, const float dt, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MarchSmem<T, LX, TY, S> sm(smem_raw);
-    const int bz = blockIdx.z;
+    MarchSmem<T, LX, TY, S, NC> sm(smem_raw);
+    const int bz = seg0 + blockIdx.z;
     const int kb = 1 + (int)(((long long)bz * g.nz) / nseg);
     const int ke = (int)(((long long)(bz + 1) * g.nz) / nseg);
     if (ke < kb) return;   // empty k segment (the host never launches one)
     sm.init(threadIdx.y * 32 + threadIdx.x);
     uint32_t ring = 0;
-    march_tile<T, LX, TY, S, SCALED, MODE>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, sc, cf, dt, blockIdx.x,
-                                           blockIdx.y, kb, ke, ring, err);
+    march_tile<T, LX, TY, S, SCALED, MODE, NC>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, sc, cf, dt, blockIdx.x,
+                                               blockIdx.y, kb, ke, ring, err);
 }
 
-// Instantiated single-grid launch shapes: (lanes per row, rows, stages).
-#define PW_TMA_CONFIGS(X) X(32, 4, 4) X(32, 8, 3) X(32, 8, 4) X(32, 8, 6) X(32, 16, 3) X(16, 4, 4) X(16, 8, 4)
+// Instantiated single-grid launch shapes: (lanes per row, rows, stages, cells
+// per thread).  8 cells per thread is instantiated for 16-bit storage only
+// (one 16-byte shared-memory access per row vector).
+#define PW_TMA_CONFIGS(X) X(32, 4, 4, 4) X(32, 8, 3, 4) X(32, 8, 4, 4) X(32, 8, 6, 4) X(32, 16, 3, 4) \
+    X(16, 4, 4, 4) X(16, 8, 4, 4) X(16, 4, 4, 8) X(16, 8, 4, 8)
 
-template <typename T, int LX, int TY, int S, bool SC, int MODE>
+template <typename T, int NC>
+constexpr bool nc_ok() { return NC == 4 || sizeof(T) == 2; }
+
+template <typename T, int LX, int TY, int S, bool SC, int MODE, int NC>
 static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1,
                                    void* o2, const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
-                                   cudaStream_t s) {
-    using L = TmaLayout<T, LX, TY, S>;
-    auto kern = tma_kernel<T, LX, TY, S, SC, MODE>;
+                                   int seg0, int seg_count, cudaStream_t s) {
+  if constexpr (!nc_ok<T, NC>()) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using L = TmaLayout<T, LX, TY, S, NC>;
+    auto kern = tma_kernel<T, LX, TY, S, SC, MODE, NC>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
+    if (seg_count <= 0) seg_count = nseg - seg0;
+    dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, seg_count);
     dim3 block(32, L::WARPS);
-    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, sc, cf, dt,
-                                      err);
+    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, seg0, sc, cf,
+                                      dt, err);
     return cudaGetLastError();
+  }
 }
 
 template <typename T, int MODE>
 static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                    const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
                                    const TmaConfig& c, cudaStream_t s) {
-#define PW_DISPATCH(LX_, TY_, S_)                                                                         \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                     \
-        return scaled ? launch_tma_inst<T, LX_, TY_, S_, true, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, \
-                                                                     c.nseg, s)                           \
-                      : launch_tma_inst<T, LX_, TY_, S_, false, MODE>(g, ox, maps, o0, o1, o2, sc, cf, dt,    \
-                                                                      err, c.nseg, s);
+#define PW_DISPATCH(LX_, TY_, S_, NC_)                                                                        \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_)                                          \
+        return scaled ? launch_tma_inst<T, LX_, TY_, S_, true, MODE, NC_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, \
+                                                                          c.nseg, c.seg0, c.seg_count, s)     \
+                      : launch_tma_inst<T, LX_, TY_, S_, false, MODE, NC_>(g, ox, maps, o0, o1, o2, sc, cf, dt,   \
+                                                                           err, c.nseg, c.seg0, c.seg_count, s);
     PW_TMA_CONFIGS(PW_DISPATCH)
 #undef PW_DISPATCH
     return cudaErrorInvalidConfiguration;

@@ -32,9 +32,9 @@ cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUten
     return cudaErrorInvalidValue;
 }
 
-bool tma_config_supported(pw_dtype_t, const TmaConfig& c) {
-#define PW_SUP(LX_, TY_, S_) \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_) return true;
+bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c) {
+#define PW_SUP(LX_, TY_, S_, NC_) \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_) return NC_ == 4 || dtype_size(dt) == 2;
     PW_TMA_CONFIGS(PW_SUP)
 #undef PW_SUP
     return false;
@@ -42,8 +42,8 @@ bool tma_config_supported(pw_dtype_t, const TmaConfig& c) {
 
 template <typename T>
 static size_t smem_t(const TmaConfig& c) {
-#define PW_SM(LX_, TY_, S_) \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_) return TmaLayout<T, LX_, TY_, S_>::SMEM;
+#define PW_SM(LX_, TY_, S_, NC_) \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_) return TmaLayout<T, LX_, TY_, S_, NC_>::SMEM;
     PW_TMA_CONFIGS(PW_SM)
 #undef PW_SM
     return 0;
@@ -61,17 +61,16 @@ size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c) {
 template <typename T>
 static int blocks_per_sm_t(const TmaConfig& c) {
     int n = 0;
-#define PW_OCC(LX_, TY_, S_)                                                                           \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_) {                                                \
-        auto kern = tma_kernel<T, LX_, TY_, S_, false, MODE_TEND>;                                     \
-        using L = TmaLayout<T, LX_, TY_, S_>;                                                          \
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM) !=   \
-            cudaSuccess)                                                                               \
-            return 0;                                                                                  \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, L::THREADS, L::SMEM) != cudaSuccess) \
-            return 0;                                                                                  \
-        return n;                                                                                      \
-    }
+#define PW_OCC(LX_, TY_, S_, NC_)                                                                      \
+    if constexpr (nc_ok<T, NC_>())                                                                     \
+        if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_) {                             \
+            auto kern = tma_kernel<T, LX_, TY_, S_, false, MODE_TEND, NC_>;                            \
+            using L = TmaLayout<T, LX_, TY_, S_, NC_>;                                                 \
+            if (set_smem_attr_once(kern, (int)L::SMEM) != cudaSuccess) return 0;                       \
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, L::THREADS, L::SMEM) != cudaSuccess) \
+                return 0;                                                                              \
+            return n;                                                                                  \
+        }
     PW_TMA_CONFIGS(PW_OCC)
 #undef PW_OCC
     return 0;
@@ -86,6 +85,6 @@ int tma_blocks_per_sm(pw_dtype_t dt, const TmaConfig& c) {
     return 0;
 }
 
-int tma_box_width(pw_dtype_t dt, int lx) { return 4 * lx + 2 * (16 / (int)dtype_size(dt)); }
+int tma_box_width(pw_dtype_t dt, int lx, int nc) { return nc * lx + 2 * (16 / (int)dtype_size(dt)); }
 
 }  // namespace pw

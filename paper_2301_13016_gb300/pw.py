@@ -52,7 +52,7 @@ SIGNATURES = [
     ("pw_create", ctypes.c_int, [ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t), ctypes.POINTER(_VP)]),
     ("pw_destroy", ctypes.c_int, [_VP]),
     ("pw_set_kernel", ctypes.c_int, [_VP, _I32]),
-    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
@@ -232,8 +232,9 @@ class PW:
     def set_kernel(self, kind):
         _check(lib().pw_set_kernel(self.h, int(kind)), "pw_set_kernel")
 
-    def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0):
-        _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(ty), int(stages), int(nseg)), "pw_set_tma_config")
+    def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0, cells=0):
+        _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg)),
+               "pw_set_tma_config")
 
     @property
     def last_kernel(self):

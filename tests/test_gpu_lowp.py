@@ -94,3 +94,36 @@ def test_normwise_errors_within_stated_bounds():
         for x, r in zip(got, ref):
             rel = np.abs(interior(x) - interior(r)).max() / np.abs(interior(r)).max()
             assert rel <= bound, (dtype, smooth, rel)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("ty,nseg", [(4, 1), (8, 3)])
+def test_eight_cells_per_thread(dtype, ty, nseg):
+    """16-bit storage with 8 cells per thread (one 16-byte access per row
+    vector): the kernel bound on a ragged tile (264 = 2 x 128 + 8 columns),
+    and agreement with the 4-cell kernel to one storage unit."""
+    nx, ny, nz = 264, 13, 10
+    c = inputs.make_coeffs(nz)
+    f = inputs.random_fields(nx, ny, nz)
+    sc = precision.suggest_scales([float(x.abs().max()) for x in f], c, dtype)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    h = pwlib.PW(g, c)
+    dev = [g.from_dense(x, scale=s) for x, s in zip(f, sc[:3])]
+    res = {}
+    for cells in (4, 8):
+        h.set_tma_config(ty, 4, nseg, lanes_x=16, cells=cells)
+        outs = [g.alloc(fill=NAN) for _ in range(3)]
+        h.tendencies(*dev, *outs, scale=sc)
+        h.sync()
+        assert h.last_kernel == 2
+        res[cells] = [g.to_dense(o).numpy() / s for o, s in zip(outs, sc[3:])]
+    qt = [g.to_dense(d, s).numpy() for d, s in zip(dev, sc[:3])]
+    ref = oracle.tendencies(*qt, c)
+    a = oracle.abs_terms(*qt, c)
+    us = precision.UNIT_ROUNDOFF[dtype]
+    for x, y, r, at, so in zip(res[8], res[4], ref, a, sc[3:]):
+        floor = 2 * precision.MIN_NORMAL[dtype] / so
+        assert np.all(np.abs(interior(x) - interior(r)) <= us * np.abs(interior(r)) + 2.0 ** -19 * interior(at) + floor)
+        assert np.all(np.abs(interior(x) - interior(y)) <= 2 * us * np.abs(interior(r)) + 2.0 ** -18 * interior(at) + 2 * floor)
+    with pytest.raises(pwlib.PwError):
+        pwlib.PW(pwlib.Grid(132, 8, 4, dtype=dtype), inputs.make_coeffs(4)).set_tma_config(4, 4, 0, lanes_x=16, cells=8)

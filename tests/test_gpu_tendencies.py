@@ -264,8 +264,9 @@ def test_mirror_antisymmetry_on_gpu():
     assert np.abs(interior(b[2]) - a[2][1:-1, 1:-1, ic]).max() <= 1e-6 * sc
 
 
-def test_host_path_matches_device_path():
-    nx, ny, nz = 256, 20, 9
+@pytest.mark.parametrize("shape", [(256, 20, 9), (128, 16, 64), (36, 8, 5)], ids=["2chunks", "8chunks", "unpipelined"])
+def test_host_path_matches_device_path(shape):
+    nx, ny, nz = shape
     c, f, g, h, dev, outs = setup(nx, ny, nz)
     run(h, dev, outs)
     a = dense_out(g, outs)
