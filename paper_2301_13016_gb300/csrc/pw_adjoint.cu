@@ -280,68 +280,72 @@ __global__ void __launch_bounds__(32 * TY)
                 auto LUT0 = [&](int dj, int di) { return lut0 ? A(P0, 3, dj, di) : 0.f; };
                 auto LVT0 = [&](int dj, int di) { return lut0 ? A(P0, 4, dj, di) : 0.f; };
 
-                float ru = 0.f, rv = 0.f, rw = 0.f;
+                // two accumulators per gradient halve the dependent FMA chains
+                float ru = 0.f, rv = 0.f, rw = 0.f, ru2 = 0.f, rv2 = 0.f, rw2 = 0.f;
                 // ---- gu
                 ru += tcx * LU0(0, 1) * (U0(0, 1) + 2.f * U0(0, 0));
-                ru += tcx * LU0(0, 0) * U0(0, -1);
+                ru2 += tcx * LU0(0, 0) * U0(0, -1);
                 ru -= tcx * LU0(0, -1) * (U0(0, -1) + 2.f * U0(0, 0));
-                ru -= tcx * LU0(0, 0) * U0(0, 1);
+                ru2 -= tcx * LU0(0, 0) * U0(0, 1);
                 ru += tcy * LU0(1, 0) * (V0(0, 0) + V0(0, 1));
-                ru -= tcy * LU0(-1, 0) * (V0(-1, 0) + V0(-1, 1));
+                ru2 -= tcy * LU0(-1, 0) * (V0(-1, 0) + V0(-1, 1));
                 if (has_p && lup) ru += c1p * A(Pp, 3, 0, 0) * (W0(0, 0) + W0(0, 1));
-                if (has_m && lutm) ru -= c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1));
+                if (has_m && lutm) ru2 -= c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1));
                 ru += tcx * LV0(0, 1) * V0(0, 0);
-                ru += tcx * LV0(-1, 1) * V0(-1, 0);
+                ru2 += tcx * LV0(-1, 1) * V0(-1, 0);
                 ru -= tcx * LV0(0, 0) * V0(0, 1);
-                ru -= tcx * LV0(-1, 0) * V0(-1, 1);
+                ru2 -= tcx * LV0(-1, 0) * V0(-1, 1);
                 ru += tcx * LW0(0, 1) * W0(0, 0);
-                ru -= tcx * LW0(0, 0) * W0(0, 1);
+                ru2 -= tcx * LW0(0, 0) * W0(0, 1);
                 if (has_m && lwm) {
                     ru += tcx * A(Pm, 5, 0, 1) * Wm(0, 0);
-                    ru -= tcx * A(Pm, 5, 0, 0) * Wm(0, 1);
+                    ru2 -= tcx * A(Pm, 5, 0, 0) * Wm(0, 1);
                 }
                 // ---- gv
                 rv += tcy * LU0(1, 0) * U0(0, 0);
-                rv += tcy * LU0(1, -1) * U0(0, -1);
+                rv2 += tcy * LU0(1, -1) * U0(0, -1);
                 rv -= tcy * LU0(0, 0) * U0(1, 0);
-                rv -= tcy * LU0(0, -1) * U0(1, -1);
+                rv2 -= tcy * LU0(0, -1) * U0(1, -1);
                 rv += tcx * LV0(0, 1) * (U0(0, 0) + U0(1, 0));
-                rv -= tcx * LV0(0, -1) * (U0(0, -1) + U0(1, -1));
+                rv2 -= tcx * LV0(0, -1) * (U0(0, -1) + U0(1, -1));
                 rv += tcy * LV0(1, 0) * (V0(1, 0) + 2.f * V0(0, 0));
-                rv += tcy * LV0(0, 0) * V0(-1, 0);
+                rv2 += tcy * LV0(0, 0) * V0(-1, 0);
                 rv -= tcy * LV0(-1, 0) * (V0(-1, 0) + 2.f * V0(0, 0));
-                rv -= tcy * LV0(0, 0) * V0(1, 0);
+                rv2 -= tcy * LV0(0, 0) * V0(1, 0);
                 if (has_p && lup) rv += c1p * A(Pp, 4, 0, 0) * (W0(0, 0) + W0(1, 0));
-                if (has_m && lutm) rv -= c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0));
+                if (has_m && lutm) rv2 -= c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0));
                 rv += tcy * LW0(1, 0) * W0(0, 0);
-                rv -= tcy * LW0(0, 0) * W0(1, 0);
+                rv2 -= tcy * LW0(0, 0) * W0(1, 0);
                 if (has_m && lwm) {
                     rv += tcy * A(Pm, 5, 1, 0) * Wm(0, 0);
-                    rv -= tcy * A(Pm, 5, 0, 0) * Wm(1, 0);
+                    rv2 -= tcy * A(Pm, 5, 0, 0) * Wm(1, 0);
                 }
                 // ---- gw
                 if (has_p) {
                     if (lup) {
                         rw += c1p * A(Pp, 3, 0, 0) * U0(0, 0);
-                        rw += c1p * A(Pp, 3, 0, -1) * U0(0, -1);
+                        rw2 += c1p * A(Pp, 3, 0, -1) * U0(0, -1);
                         rw += c1p * A(Pp, 4, 0, 0) * V0(0, 0);
-                        rw += c1p * A(Pp, 4, -1, 0) * V0(-1, 0);
+                        rw2 += c1p * A(Pp, 4, -1, 0) * V0(-1, 0);
                     }
                     rw -= c2 * LUT0(0, 0) * Up(0, 0);
-                    rw -= c2 * LUT0(0, -1) * Up(0, -1);
+                    rw2 -= c2 * LUT0(0, -1) * Up(0, -1);
                     rw -= c2 * LVT0(0, 0) * Vp(0, 0);
-                    rw -= c2 * LVT0(-1, 0) * Vp(-1, 0);
+                    rw2 -= c2 * LVT0(-1, 0) * Vp(-1, 0);
                     rw += tcx * LW0(0, 1) * (U0(0, 0) + Up(0, 0));
-                    rw -= tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1));
+                    rw2 -= tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1));
                     rw += tcy * LW0(1, 0) * (V0(0, 0) + Vp(0, 0));
-                    rw -= tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0));
+                    rw2 -= tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0));
                     if (lwp) rw += d1p * A(Pp, 5, 0, 0) * (Wp(0, 0) + 2.f * W0(0, 0));
-                    rw -= d2 * LW0(0, 0) * Wp(0, 0);
+                    rw2 -= d2 * LW0(0, 0) * Wp(0, 0);
                 }
                 if (has_m) {
                     rw += d1 * LW0(0, 0) * Wm(0, 0);
-                    if (lwm) rw -= d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0));
+                    if (lwm) rw2 -= d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0));
                 }
+                ru += ru2;
+                rv += rv2;
+                rw += rw2;
 
                 if (J <= g.ny && I <= g.nx) {
                     const long long o = g.origin + (long long)K * g.pk + (long long)J * g.pj + I;
