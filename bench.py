@@ -37,7 +37,8 @@ FLOPS_PER_CELL = 63              # 21 useful FLOPs per field (Sec. 4 op structur
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
                   for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
-FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "precision", "batch", "adjoint", "latency64"]
+FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16", "precision",
+         "batch", "adjoint", "latency64"]
 
 
 def parse():
@@ -388,7 +389,13 @@ def form_tend_lowp(args, dtype):
                 "gpu_launches": args.steps})
 
 
-def form_step(args, dtype):
+STEP2_SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (16, 3, 1)]
+
+
+def form_step(args, dtype, spp=1):
+    """Fused forward-Euler steps on 2048 x 2048 x 64: one step per kernel
+    pass (spp = 1, halo-1 grid) or two (spp = 2, halo-2 grid, every
+    instantiated launch shape timed; the value is the automatic shape's)."""
     import paper_2301_13016_gb300 as pwlib
     from paper_2301_13016_gb300 import inputs, precision
     nx = ny = 2048
@@ -396,30 +403,50 @@ def form_step(args, dtype):
     stream = torch.cuda.current_stream()
     ref = _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
     c = inputs.make_coeffs(nz)
-    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype, halo=spp)
     h = pwlib.PW(g, c)
+    h.set_step_blocking(spp)
     dense = inputs.smooth_fields(nx, ny, nz, w_zero=True, device="cuda")
     sc = precision.suggest_scales([max(float(x.abs().max()), 1.0) for x in dense], c, dtype)[:3]
     q = [g.from_dense(x, scale=s) for x, s in zip(dense, sc)]
     del dense
     tmp = [g.alloc() for _ in range(3)]
-    nsteps = args.steps if args.steps % 2 == 0 else args.steps + 1   # even: no final copy-back
+    nsteps = args.steps if args.steps % (2 * spp) == 0 else args.steps + 2 * spp - args.steps % (2 * spp)
     f = lambda: h.step(*q, *tmp, 0.0, nsteps, scale=sc, stream=stream)
-    h.step(*q, *tmp, 0.0, 2, scale=sc, stream=stream)
-    ms = _events_ms(f, 1, stream) / nsteps
-    h.sync(stream)
+
+    def timed():
+        h.step(*q, *tmp, 0.0, 2 * spp, scale=sc, stream=stream)
+        ms_ = _events_ms(f, 1, stream) / nsteps
+        h.sync(stream)
+        return ms_
+
+    shapes = {}
+    if spp == 2:
+        for shp in STEP2_SHAPES:
+            h.set_step_blocking(2, ty=shp[0], stages=shp[1], ctas_per_sm=shp[2])
+            shapes["ty%d_s%d_c%d" % shp] = g.cells / (timed() / 1e3) / 1e9
+        h.set_step_blocking(2)
+    ms = timed()
+    kernel = h.last_kernel
     val = g.cells / (ms / 1e3) / 1e9
     es = 4 if dtype == "f32" else 2
+    bpcs = 6 * es / spp
     peak, kind = measured_peak()
-    achieved = 6 * es * g.cells / (ms / 1e3) / 1e9
-    _form_line(args, "step" if dtype == "f32" else f"step-{dtype}",
-               f"PW fused forward-Euler step, Gcell-steps/s, {dtype.upper()} state", val, "Gcell-steps/s",
+    achieved = bpcs * g.cells / (ms / 1e3) / 1e9
+    name = ("step" if spp == 1 else "step2") + ("" if dtype == "f32" else f"-{dtype}")
+    extra = {"dtype": dtype, "ms_per_step": ms, "vs_fp32_tend_form": val / ref, "fp32_tend_gcells": ref,
+             "steps_per_pass": spp, "last_kernel": kernel,
+             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell_step": bpcs},
+             "gpu_launches": nsteps // spp + 3}
+    if shapes:
+        extra["shapes_gcell_steps"] = shapes
+    _form_line(args, name,
+               f"PW fused forward-Euler step, Gcell-steps/s, {dtype.upper()} state, {spp} step(s) per pass", val,
+               "Gcell-steps/s",
                {"workload": f"{nx}x{ny}x{nz} smooth field (w = 0 initially), {nsteps} fused steps per call "
-                            "(dt = 0 keeps the state fixed for timing)", "scales": list(sc)},
-               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_tend_form": val / ref, "fp32_tend_gcells": ref,
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell_step": 6 * es},
-                "gpu_launches": nsteps + 3})
+                            f"(dt = 0 keeps the state fixed for timing), halo {spp}", "scales": list(sc)},
+               extra)
 
 
 def form_precision(args):
@@ -444,9 +471,10 @@ def form_precision(args):
             ref = list(oracle.step(*ref, c, 1.0, every))
             refs.append(ref)
         res = {}
-        for dtype in ("f32", "bf16", "f16"):
-            g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+        for dtype, spp in (("f32", 1), ("bf16", 1), ("f16", 1), ("bf16", 2), ("f16", 2)):
+            g = pwlib.Grid(nx, ny, nz, dtype=dtype, halo=spp)
             h = pwlib.PW(g, c)
+            h.set_step_blocking(spp)
             sc = precision.suggest_scales([max(float(x.abs().max()), 1.0) for x in dense], c, dtype)[:3]
             q = [g.from_dense(x, scale=s) for x, s in zip(dense, sc)]
             tmp = [g.alloc() for _ in range(3)]
@@ -465,7 +493,7 @@ def form_precision(args):
                 errs.append(row)
                 if not np.isfinite(umax) or umax > 1e3 * 10:
                     break
-            res[dtype] = errs
+            res[dtype if spp == 1 else f"{dtype}-2step"] = errs
         out[field] = res
     _form_line(args, "precision", "max|err|/max|ref| vs FP64 oracle per 10 steps, 100 fused Euler steps", None,
                "relative error", {"workload": f"{nx}x{ny}x{nz}, dt = 1 s; smooth field with w = 0 initially, and "
@@ -628,6 +656,8 @@ def main():
         elif rank == 0:
             {"tend-bf16": lambda: form_tend_lowp(args, "bf16"), "tend-f16": lambda: form_tend_lowp(args, "f16"),
              "step": lambda: form_step(args, "f32"), "step-bf16": lambda: form_step(args, "bf16"),
+             "step2": lambda: form_step(args, "f32", 2), "step2-bf16": lambda: form_step(args, "bf16", 2),
+             "step2-f16": lambda: form_step(args, "f16", 2),
              "precision": lambda: form_precision(args), "batch": lambda: form_batch(args),
              "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args)}[args.form]()
     finally:

@@ -133,6 +133,24 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
                               int32_t nseg);
 
 /*
+ * Temporal blocking of pw_step.  steps_per_pass: 1 = one step per kernel
+ * pass; 2 = two steps per pass (needs the TMA path, a lateral halo >= 2 and
+ * interior rows starting >= 7 elements into their padded row, else pw_step
+ * returns PW_ERR_UNSUPPORTED); 0 = automatic, which is one step per pass:
+ * the two-step pass halves the HBM bytes per step but recomputes the
+ * intermediate state on a one-cell border of every tile and is bound by
+ * instruction issue, so on GB300 it is slower per step.  Launch
+ * shape of the two-step kernel (0 = automatic): ty = rows of the intermediate
+ * state per CTA (ty - 2 output rows), stages = input planes in flight,
+ * ctas_per_sm = the register budget (1: up to 255 registers a thread; 2: 128,
+ * part of the state in local memory), nseg = CTAs along z.  Instantiated
+ * (ty, stages, ctas_per_sm): (8,3,1) (8,3,2) (8,4,1) (16,3,1); others give
+ * PW_ERR_UNSUPPORTED.  Automatic shape: (8, 3, 1).
+ */
+pw_status_t pw_set_step_blocking(pw_handle_t h, int32_t steps_per_pass, int32_t ty, int32_t stages,
+                                 int32_t ctas_per_sm, int32_t nseg);
+
+/*
  * Source terms su, sv, sw of the PW scheme (Sec. 2.2; arithmetic shape
  * Sec. 4) from u, v, w, all in the handle's layout and dtype, halo cells of
  * the inputs used as given (refresh them first, e.g. with
@@ -167,10 +185,17 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
  * scratch fields of the same layout (contents overwritten).  Each step is one
  * fused kernel pass that reads the state once and writes the next state once,
  * periodic images of the boundary cells included; the two buffer sets
- * alternate, and an odd nsteps ends with a device copy back into (u, v, w).
+ * alternate, and an odd number of passes ends with a device copy back into
+ * (u, v, w).  With a lateral halo of at least 2 (and the TMA path), a pass
+ * can advance two steps (temporal blocking, opt-in via pw_set_step_blocking): the
+ * intermediate state stays on chip in FP32, so the bytes per step halve;
+ * FP32 results are identical to single-step passes, and 16-bit storage is
+ * rounded once per two steps instead of every step.
  * scale: NULL or 3 floats {s_u, s_v, s_w}: physical = stored * s (for 16-bit
- * storage; the state is rounded to the storage type after every step).
+ * storage; the state is rounded to the storage type after every pass).
  * All six pointers must be distinct.  nsteps = 0 only refreshes the halos.
+ * pw_last_kernel reports 1 (generic), 2 (TMA, one step per pass) or 3 (TMA,
+ * two steps per pass, with one single-step pass for an odd remainder).
  */
 pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void *tmp_v, void *tmp_w,
                     float dt, int32_t nsteps, const float *scale, pw_stream_t stream);
@@ -336,8 +361,9 @@ const char *pw_last_error(void);
 /* Static name of a status code. */
 const char *pw_status_string(pw_status_t s);
 
-/* Which kernel the last pw_tendencies call on this handle launched:
- * 1 = generic, 2 = TMA k-march, 0 = none yet. */
+/* Which kernel the last pw_tendencies, pw_step or pw_adjoint call on this
+ * handle launched: 1 = generic, 2 = TMA k-march, 3 = two-step TMA k-march
+ * (pw_step), 0 = none yet. */
 int32_t pw_last_kernel(pw_handle_t h);
 
 #ifdef __cplusplus

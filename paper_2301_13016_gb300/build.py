@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpw.so")
-SOURCES = ["pw_api.cu", "pw_tend.cu", "pw_step.cu", "pw_adjoint.cu", "pw_batch.cu", "pw_halo.cu", "pw_norms.cu", "pw_selftest.cu", "pw_noalloc.cu"]
+SOURCES = ["pw_api.cu", "pw_tend.cu", "pw_step.cu", "pw_step2.cu", "pw_adjoint.cu", "pw_batch.cu", "pw_halo.cu", "pw_norms.cu", "pw_selftest.cu", "pw_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
     [os.path.join(ROOT, "include", "pw.h")]
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -58,7 +58,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 struct MapCacheEntry {
     const void* ptr = nullptr;
-    int ty = 0, lx = 0, nc = 0;
+    int box_w = 0, box_h = 0;
     CUtensorMap map;
 };
 
@@ -77,6 +77,9 @@ struct pw_handle_s {
     int last_kernel = 0;
     TmaConfig tma_user{0, 0, 0, 0};
     TmaConfig tma_auto{0, 0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
+    int steps_per_pass = 0;           // pw_step temporal blocking: 0 auto (= 1), 1, 2
+    Step2Config step2_user{0, 0, 0, 0};
+    Step2Config step2_auto{0, 0, 0, 0};   // ty == 0: not chosen yet
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
     // pw_tendencies_host staging and its copy / compute pipeline
@@ -144,29 +147,47 @@ bool pw::tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
 
 bool pw::aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
-                              int nc = 4) {
+// Tensor map of a field for a box of box_w x box_h elements, from the
+// handle's cache of recently encoded maps.
+static pw_status_t encode_map_box(pw_handle_t h, const void* ptr, int box_w, int box_h, CUtensorMap* out) {
     for (auto& c : h->maps)
-        if (c.ptr == ptr && c.ty == ty && c.lx == lx && c.nc == nc) {
+        if (c.ptr == ptr && c.box_w == box_w && c.box_h == box_h) {
             *out = c.map;
             return PW_OK;
         }
     MapCacheEntry& e = h->maps[h->map_next];
     h->map_next = (h->map_next + 1) % (int)(sizeof(h->maps) / sizeof(h->maps[0]));
-    pw_status_t st = encode_tensor_map(h->grid, ptr, ox, lx, ty, out, nc);
+    pw_status_t st = encode_tensor_map_box(h->grid, ptr, box_w, box_h, out);
     if (st != PW_OK) return st;
     e.ptr = ptr;
-    e.ty = ty;
-    e.lx = lx;
-    e.nc = nc;
+    e.box_w = box_w;
+    e.box_h = box_h;
     e.map = *out;
     return PW_OK;
 }
 
+// Tensor map for the single-step k-march shape (lx lanes x nc cells, ty rows).
+static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
+                              int nc = 4) {
+    (void)ox;
+    return encode_map_box(h, ptr, tma_box_width(h->grid.dtype, lx, nc), ty + 2, out);
+}
+
 pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
                                   int nc) {
+    (void)ox;
+    return encode_tensor_map_box(g, ptr, tma_box_width(g.dtype, lx, nc), ty + 2, out);
+}
+
+// 3D map of one field: x = the padded row from its first element (element
+// i = 0 at x = ox), y = rows from j = 1-halo, z = levels 0..nz+1.  Boxes of
+// box_w x box_h x 1; out-of-range elements read as zero.
+pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out) {
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    int ox = 0;
+    const char* why = "";
+    if (!tma_layout_ok(g, &ox, &why)) return fail(PW_ERR_UNSUPPORTED, "layout not TMA-eligible: %s", why);
     const size_t es = dtype_size(g.dtype);
     CUtensorMapDataType dt = g.dtype == PW_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : g.dtype == PW_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -174,7 +195,7 @@ pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, i
     cuuint64_t dims[3] = {(cuuint64_t)(ox + g.nx + g.halo + 1), (cuuint64_t)(g.ny + 2 * g.halo),
                           (cuuint64_t)(g.nz + 2)};
     cuuint64_t strides[2] = {(cuuint64_t)(g.pitch_j * es), (cuuint64_t)(g.pitch_k * es)};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(g.dtype, lx, nc), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(out, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -358,6 +379,45 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
     h->tma_auto = TmaConfig{0, 0, 0, 0};
     for (auto& m : h->maps) m.ptr = nullptr;
     return PW_OK;
+}
+
+pw_status_t pw_set_step_blocking(pw_handle_t h, int32_t steps_per_pass, int32_t ty, int32_t stages,
+                                 int32_t ctas_per_sm, int32_t nseg) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (steps_per_pass < 0 || steps_per_pass > 2) return fail(PW_ERR_ARG, "steps_per_pass must be 0, 1 or 2");
+    if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
+    Step2Config c{ty ? ty : 8, stages ? stages : 3, 1, ctas_per_sm ? ctas_per_sm : 1};
+    if (!step2_config_supported(c))
+        return fail(PW_ERR_UNSUPPORTED, "no two-step kernel instance for ty=%d stages=%d ctas_per_sm=%d", c.ty,
+                    c.stages, c.minb);
+    h->steps_per_pass = steps_per_pass;
+    h->step2_user = Step2Config{ty, stages, nseg, ctas_per_sm};
+    h->step2_auto = Step2Config{0, 0, 0, 0};
+    return PW_OK;
+}
+
+// Launch shape of the two-step kernel: user overrides, else 8 rows, 3 stages,
+// the full register budget (one CTA per SM), and k segments doubled until
+// about two waves of CTAs cover the SMs (each segment keeps >= 8 levels).
+static Step2Config choose_step2(pw_handle_t h) {
+    if (h->step2_auto.ty) return h->step2_auto;
+    const Step2Config& u = h->step2_user;
+    Step2Config c{u.ty ? u.ty : 8, u.stages ? u.stages : 3, 1, u.minb ? u.minb : 1};
+    if (u.nseg) {
+        c.nseg = u.nseg;
+    } else {
+        const long long tiles = (long long)((h->grid.nx + step2_tile_cols() - 1) / step2_tile_cols()) *
+                                ((h->grid.ny + c.ty - 3) / (c.ty - 2));
+        int bps = step2_blocks_per_sm(h->grid.dtype, c);
+        if (bps < 1) bps = 1;
+        const long long slots = (long long)h->num_sms * bps;
+        int nseg = 1;
+        while (tiles * nseg < 2 * slots && h->grid.nz / (nseg * 2) >= 8) nseg *= 2;
+        c.nseg = nseg;
+    }
+    if (c.nseg > h->grid.nz / 2) c.nseg = std::max(1, h->grid.nz / 2);
+    h->step2_auto = c;
+    return c;
 }
 
 int32_t pw_last_kernel(pw_handle_t h) { return h ? h->last_kernel : 0; }
@@ -564,32 +624,52 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
         if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
     }
     const bool use_tma = (h->kernel_kind == 2) || (h->kernel_kind == 0 && layout_ok && ptrs_ok);
+    // two steps per pass: TMA path, a lateral halo >= 2, and interior rows
+    // starting at least 7 elements into their padded row (the q0 box begins
+    // 7 columns before the first interior column)
+    const bool tb2_ok = use_tma && g.halo >= 2 && ox >= 7;
+    if (h->steps_per_pass == 2 && nsteps >= 2 && !tb2_ok)
+        return fail(PW_ERR_UNSUPPORTED, "two steps per pass need the TMA path, a halo >= 2 and >= 7 columns before "
+                                        "the interior in each padded row");
+    // automatic (0) is one step per pass: on GB300 the two-step pass is bound
+    // by instruction issue, not HBM, and runs slower per step
+    const bool use_tb2 = tb2_ok && h->steps_per_pass == 2;
     TmaConfig c{};
     if (use_tma) c = choose_tma(h);
-    for (int n = 0; n < nsteps; ++n) {
-        void** src = (n % 2 == 0) ? bufs : bufs + 3;
-        void** dst = (n % 2 == 0) ? bufs + 3 : bufs;
+    Step2Config c2{};
+    if (use_tb2 && nsteps >= 2) c2 = choose_step2(h);
+    int done = 0, passes = 0, kind = use_tma ? 2 : 1;
+    while (done < nsteps) {
+        void** src = (passes % 2 == 0) ? bufs : bufs + 3;
+        void** dst = (passes % 2 == 0) ? bufs + 3 : bufs;
         cudaError_t e;
-        if (use_tma) {
+        if (use_tb2 && nsteps - done >= 2) {
+            CUtensorMap maps[3];
+            for (int q = 0; q < 3; ++q) {
+                pw_status_t st = encode_map_box(h, src[q], step2_box_width(), c2.ty + 2, &maps[q]);
+                if (st != PW_OK) return st;
+            }
+            e = launch_step2_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c2, s);
+            done += 2;
+            kind = 3;
+        } else if (use_tma) {
             CUtensorMap maps[3];
             for (int q = 0; q < 3; ++q) {
                 pw_status_t st = encode_map(h, src[q], ox, c.lx, c.ty, &maps[q], c.nc);
                 if (st != PW_OK) return st;
             }
             e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);
+            done += 1;
         } else {
             e = launch_step_generic(dtp, g, src[0], src[1], src[2], dst[0], dst[1], dst[2], sc, scaled, cf, dt,
                                     h->num_sms, s);
+            done += 1;
         }
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        if (g.halo != 1)   // the kernel writes the images of a one-cell halo only
-            for (int q = 0; q < 3; ++q) {
-                e = launch_fill_halo(dtp, g, dst[q], h->num_sms, s);
-                if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
-            }
+        ++passes;
     }
-    h->last_kernel = use_tma ? 2 : 1;
-    if (nsteps % 2 == 1) {   // the last state is in the scratch buffers: copy levels 1..nz back
+    h->last_kernel = kind;
+    if (passes % 2 == 1) {   // the last state is in the scratch buffers: copy levels 1..nz back
         const size_t es = dtype_size(dtp);
         const pw_grid_t& gg = h->grid;
         const size_t lo = (size_t)(gg.origin + gg.pitch_k + (long long)(1 - gg.halo) * gg.pitch_j + 1 - gg.halo);

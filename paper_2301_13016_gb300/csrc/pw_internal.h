@@ -41,6 +41,14 @@ struct TmaConfig {
     int seg_count = 0;  // segments to launch (0 = all nseg)
 };
 
+// Launch shape of the two-step (temporal blocking) k-march kernel.
+struct Step2Config {
+    int ty;      // q1 rows per CTA (q2 rows: ty - 2)
+    int stages;  // q0 planes resident or in flight per CTA
+    int nseg;    // k segments
+    int minb;    // register budget: 1 or 2 resident CTAs per SM
+};
+
 size_t dtype_size(pw_dtype_t t);
 
 cudaError_t launch_tend_generic(pw_dtype_t dt, const GridDev& g, const void* u, const void* v, const void* w,
@@ -58,13 +66,24 @@ cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUten
                             int* err, const TmaConfig& c, cudaStream_t s);
 
 // Forward-Euler step kernels: (nu, nv, nw) = (u, v, w) + tstep * s(u, v, w),
-// interior levels 1..nz plus the periodic images of boundary cells (halo 1).
+// interior levels 1..nz plus the periodic images of boundary cells in the halo.
 cudaError_t launch_step_generic(pw_dtype_t dt, const GridDev& g, const void* u, const void* v, const void* w,
                                 void* nu, void* nv, void* nw, const Scales& sc, bool scaled, const CoefDev& cf,
                                 float tstep, int num_sms, cudaStream_t s);
 cudaError_t launch_step_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
                             void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
                             const TmaConfig& c, cudaStream_t s);
+
+// Two forward-Euler steps per pass (temporal blocking): (nu, nv, nw) = q2
+// with q1 = q + tstep*s(q), q2 = q1 + tstep*s(q1); needs a lateral halo of
+// at least 2 and maps encoded with box step2_box_width() x (ty + 2).
+cudaError_t launch_step2_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
+                             void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                             const Step2Config& c, cudaStream_t s);
+bool step2_config_supported(const Step2Config& c);
+int step2_box_width();
+int step2_tile_cols();
+int step2_blocks_per_sm(pw_dtype_t dt, const Step2Config& c);
 
 // Adjoint gather kernel (FP32 fields): g = [g | l | 0] + alpha * J(u,v,w)^T l.
 cudaError_t launch_adjoint(const GridDev& g, const float* u, const float* v, const float* w, const float* lu,
@@ -107,5 +126,7 @@ bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why);
 bool aligned16(const void* p);
 pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
                               int nc = 4);
+// Same with an explicit box (box_w elements along x, box_h rows).
+pw_status_t encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out);
 
 }  // namespace pw

@@ -2,8 +2,8 @@
 // on the storage type T and on what the epilogue does with the source terms:
 //   MODE_TEND: store su, sv, sw;
 //   MODE_STEP: store the forward-Euler update q + dt*s of u, v, w, together
-//              with the periodic images of the boundary cells (halo 1), so the
-//              next step reads a complete halo.
+//              with the periodic images of the boundary cells in the lateral
+//              halo, so the next step reads a complete halo.
 // Instantiated by pw_tend.cu (MODE_TEND) and pw_step.cu (MODE_STEP).
 #pragma once
 
@@ -14,9 +14,8 @@ namespace pw {
 
 enum { MODE_TEND = 0, MODE_STEP = 1 };
 
-// Writes the three outputs of one cell or one row vector of 4 cells, plus the
-// periodic images (MODE_STEP, halo 1) when the cells lie on the lateral
-// boundary.  o = offset of (k, j, i0); cells i0..i0+n-1.
+// Writes the three outputs of one cell or one row vector of N cells, plus the
+// periodic images (MODE_STEP) when the cells lie near the lateral boundary.  o = offset of (k, j, i0); cells i0..i0+n-1.
 template <typename T, int MODE>
 struct Epilogue;
 
@@ -38,6 +37,10 @@ struct Epilogue<T, MODE_TEND> {
     }
 };
 
+// MODE_STEP writes, with each cell, its periodic images in the lateral halo
+// of depth H = g.halo (H <= nx and H <= ny, which the grid check enforces):
+// cell i <= H also goes to i + nx, cell i > nx - H to i - nx, and likewise in
+// y, corners included, so the next step reads a complete halo.
 template <typename T>
 struct Epilogue<T, MODE_STEP> {
     // one cell (j, i) at offset o
@@ -50,11 +53,11 @@ struct Epilogue<T, MODE_STEP> {
             o2[p] = tc;
         };
         put(o);
-        if (g.halo != 1) return;   // deeper halos are refreshed by the halo kernel
-        const long long dxp = (i == 1) ? (long long)g.nx : 0;        // image at i = nx+1
-        const long long dxm = (i == g.nx) ? -(long long)g.nx : 0;    // image at i = 0
-        const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
-        const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
+        const int H = g.halo;
+        const long long dxp = (i <= H) ? (long long)g.nx : 0;             // image at i + nx
+        const long long dxm = (i > g.nx - H) ? -(long long)g.nx : 0;      // image at i - nx
+        const long long dyp = (j <= H) ? (long long)g.ny * g.pj : 0;
+        const long long dym = (j > g.ny - H) ? -(long long)g.ny * g.pj : 0;
         if (dxp) put(o + dxp);
         if (dxm) put(o + dxm);
         if (dyp) {
@@ -76,10 +79,11 @@ struct Epilogue<T, MODE_STEP> {
         storev<N>(o0 + o, a);
         storev<N>(o1 + o, b);
         storev<N>(o2 + o, c);
-        if (g.halo != 1) return;
-        const bool west = (i0 == 1), east = (i0 + N - 1 == g.nx);
-        const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
-        const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
+        const int H = g.halo;
+        const bool west = (i0 <= H), east = (i0 + N - 1 > g.nx - H);
+        const long long dyp = (j <= H) ? (long long)g.ny * g.pj : 0;
+        const long long dym = (j > g.ny - H) ? -(long long)g.ny * g.pj : 0;
+        if (!west && !east && !dyp && !dym) return;
         auto cell = [&](long long p, int q) {
             o0[p] = Store<T>::from_f(a[q]);
             o1[p] = Store<T>::from_f(b[q]);
@@ -95,8 +99,11 @@ struct Epilogue<T, MODE_STEP> {
                 storev<N>(o1 + p, b);
                 storev<N>(o2 + p, c);
             }
-            if (west) cell(p + g.nx, 0);                   // cell i = 1 -> i = nx+1
-            if (east) cell(p + (N - 1) - g.nx, N - 1);     // cell i = nx -> i = 0
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                if (west && i0 + q <= H) cell(p + q + g.nx, q);          // i -> i + nx
+                if (east && i0 + q > g.nx - H) cell(p + q - g.nx, q);    // i -> i - nx
+            }
         }
     }
 };
@@ -175,6 +182,186 @@ static cudaError_t launch_generic_mode(const GridDev& g, const void* u, const vo
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// One level of a k-march for the NC consecutive cells of one thread (shared
+// by every k-march kernel: single step, two-step temporal blocking, batch).
+//
+// MarchRegs is what a thread carries from level kk to kk+1: the level-kk rows
+// it loaded as level kk+1 on the previous step, the level kk-1 values at its
+// cells (a rolling window in z) and the three vertical pair sums of the upper
+// fluxes, which are the lower pair sums of the next level.
+template <int NC>
+struct MarchRegs {
+    float u0[NC], v0[NC], vs[NC], w0[NC];   // level kk: u, v, w in row r; vs = v in row r-1
+    float ud[NC], vd[NC], wd[NC];           // level kk-1 at the cells
+    float pzu[NC], pzv[NC], pzw[NC];        // lower vertical pair sums of level kk
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            ud[c] = vd[c] = wd[c] = pzu[c] = pzv[c] = pzw[c] = 0.f;
+            u0[c] = v0[c] = vs[c] = w0[c] = 0.f;
+        }
+    }
+};
+
+enum { F_U = 0, F_V = 1, F_W = 2 };
+
+// Source terms (Sec. 2.2) of level kk, handed to `out`, then the roll of `st`
+// to level kk+1.  The data source is abstract:
+//   row(f, up, dr, o)  the thread's NC values of field f (F_U, F_V, F_W) in
+//                      row r+dr of level kk+up (up = 0 or 1)
+//   edge(f, up, dr)    the x neighbour beyond the row's ends: x = -1 for the
+//                      row's first lane, x = NC*LX for its last lane
+//   out(ru, rv, rw, u, v, w)   the source terms and the level-kk values
+// first:   kk is the first level of the march (its rows are loaded here)
+// have_up: level kk+1 exists (kk < nz): the upper vertical fluxes and sw
+// compute: evaluate the source terms (else they are zero: k = 1, or a level
+//          that only primes the carried state)
+// x neighbours within a row come from the adjacent lanes by warp shuffles
+// (LX lanes per row).  Pair sums along x are shared by neighbouring cells.
+template <int NC, int LX, class Row, class Edge, class Out>
+__device__ __forceinline__ void march_level(MarchRegs<NC>& st, const Row& row, const Edge& edge, const Out& out,
+                                            const int xl, const bool first, const bool have_up, const bool compute,
+                                            const float tcx, const float tcy, const float* __restrict__ tz,
+                                            const int kk, const int nzp2) {
+    const unsigned FULL = 0xffffffffu;
+    // x-neighbours of a row vector: value at x = -1 (m) and x = NC (p)
+    auto nbr_m = [&](const float (&x)[NC], float e) {
+        float m = __shfl_up_sync(FULL, x[NC - 1], 1, LX);
+        return xl == 0 ? e : m;
+    };
+    auto nbr_p = [&](const float (&x)[NC], float e) {
+        float p = __shfl_down_sync(FULL, x[0], 1, LX);
+        return xl == LX - 1 ? e : p;
+    };
+    if (first) {
+        row(F_U, 0, 0, st.u0);
+        row(F_V, 0, 0, st.v0);
+        row(F_V, 0, -1, st.vs);
+        row(F_W, 0, 0, st.w0);
+    }
+    float wn[NC];
+    row(F_W, 0, 1, wn);
+    const float ew = edge(F_W, 0, 0);
+    float W[NC + 2];   // x = -1..NC
+    W[0] = nbr_m(st.w0, ew);
+    W[NC + 1] = nbr_p(st.w0, ew);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) W[c + 1] = st.w0[c];
+
+    // level kk+1 rows (upper terms; carried into the next step)
+    float uu[NC], vu[NC], vus[NC], wu[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) uu[c] = vu[c] = vus[c] = wu[c] = 0.f;
+    float euu = 0.f;
+    if (have_up) {
+        row(F_U, 1, 0, uu);
+        row(F_V, 1, 0, vu);
+        row(F_V, 1, -1, vus);
+        row(F_W, 1, 0, wu);
+        euu = edge(F_U, 1, 0);
+    }
+    // upper vertical pair sums of level kk = lower ones of level kk+1
+    float pzu_n[NC], pzv_n[NC], pzw_n[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        pzu_n[c] = W[c + 1] + W[c + 2];    // w(k,i) + w(k,i+1)
+        pzv_n[c] = st.w0[c] + wn[c];       // w(k,j) + w(k,j+1)
+        pzw_n[c] = st.w0[c] + wu[c];       // w(k) + w(k+1)
+    }
+
+    float ru[NC], rv[NC], rw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ru[c] = rv[c] = rw[c] = 0.f;
+    if (compute) {
+        float us[NC], un[NC], vn[NC], ws[NC];
+        row(F_U, 0, -1, us);
+        row(F_U, 0, 1, un);
+        row(F_V, 0, 1, vn);
+        row(F_W, 0, -1, ws);
+        const float eu = edge(F_U, 0, 0);
+        const float ev = edge(F_V, 0, 0);
+        const float eun = edge(F_U, 0, 1);
+        const float evs = edge(F_V, 0, -1);
+        float U[NC + 2], V[NC + 2];    // x = -1..NC
+        float UN[NC + 1], UU[NC + 1];  // x = -1..NC-1
+        float VS[NC + 1];              // x = 0..NC
+        U[0] = nbr_m(st.u0, eu);
+        U[NC + 1] = nbr_p(st.u0, eu);
+        V[0] = nbr_m(st.v0, ev);
+        V[NC + 1] = nbr_p(st.v0, ev);
+        UN[0] = nbr_m(un, eun);
+        UU[0] = nbr_m(uu, euu);
+        VS[NC] = nbr_p(st.vs, evs);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            U[c + 1] = st.u0[c];
+            V[c + 1] = st.v0[c];
+            UN[c + 1] = un[c];
+            UU[c + 1] = uu[c];
+            VS[c] = st.vs[c];
+        }
+
+        // pair sums along x shared by neighbouring cells: index c is the
+        // pair (x = c-1, c)
+        float pxu[NC + 1], qx[NC + 1], rx[NC + 1], pxv[NC], pys[NC];
+#pragma unroll
+        for (int c = 0; c < NC + 1; ++c) {
+            pxu[c] = U[c] + U[c + 1];     // u(i-1) + u(i)
+            qx[c] = U[c] + UN[c];         // u(j,i-1) + u(j+1,i-1)
+            rx[c] = U[c] + UU[c];         // u(k,i-1) + u(k+1,i-1)
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            pxv[c] = V[c + 1] + V[c + 2];  // v(j,i) + v(j,i+1)
+            pys[c] = VS[c] + VS[c + 1];    // v(j-1,i) + v(j-1,i+1)
+        }
+        const float tz1 = __ldg(tz + kk);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            // su
+            float x = tcx * fmaf(-U[c + 2], pxu[c + 1], U[c] * pxu[c]);
+            x = fmaf(tcy, fmaf(-un[c], pxv[c], us[c] * pys[c]), x);
+            ru[c] = fmaf(tz1, st.ud[c] * st.pzu[c], x);
+            // sv
+            float y = tcx * fmaf(-V[c + 2], qx[c + 1], V[c] * qx[c]);
+            y = fmaf(tcy, fmaf(-vn[c], V[c + 1] + vn[c], st.vs[c] * (V[c + 1] + st.vs[c])), y);
+            rv[c] = fmaf(tz1, st.vd[c] * st.pzv[c], y);
+        }
+        if (have_up) {   // kk < nz: upper vertical fluxes and sw
+            const float tz2 = __ldg(tz + nzp2 + kk);
+            const float td1 = __ldg(tz + 2 * nzp2 + kk);
+            const float td2 = __ldg(tz + 3 * nzp2 + kk);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                ru[c] = fmaf(-tz2, uu[c] * pzu_n[c], ru[c]);
+                rv[c] = fmaf(-tz2, vu[c] * pzv_n[c], rv[c]);
+                float z = tcx * fmaf(-W[c + 2], rx[c + 1], W[c] * rx[c]);
+                z = fmaf(tcy, fmaf(-wn[c], V[c + 1] + vu[c], ws[c] * (st.vs[c] + vus[c])), z);
+                z = fmaf(td1, st.wd[c] * st.pzw[c], z);
+                rw[c] = fmaf(-td2, wu[c] * pzw_n[c], z);
+            }
+        }
+    }
+
+    out(ru, rv, rw, st.u0, st.v0, st.w0);
+
+    // roll: level kk becomes level k-1, level kk+1 becomes level kk
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        st.ud[c] = st.u0[c];
+        st.vd[c] = st.v0[c];
+        st.wd[c] = st.w0[c];
+        st.pzu[c] = pzu_n[c];
+        st.pzv[c] = pzv_n[c];
+        st.pzw[c] = pzw_n[c];
+        st.u0[c] = uu[c];
+        st.v0[c] = vu[c];
+        st.vs[c] = vus[c];
+        st.w0[c] = wu[c];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // TMA k-march.
@@ -330,8 +517,6 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC>& sm
     const float tcx = cf.tcx, tcy = cf.tcy;
     const int nzp2 = nz + 2;
     const unsigned FULL = 0xffffffffu;
-    const float su_in = sc.in[0], sv_in = sc.in[1], sw_in = sc.in[2];
-
     auto ld = [&](const T* p, float (&o)[NC], float s) {
         loadv<NC>(p, o);
         if (SCALED) {
@@ -343,30 +528,24 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC>& sm
         float x = Store<T>::to_f(*p);
         return SCALED ? x * s : x;
     };
-    // x-neighbours of a row vector: value at x = -1 (m) and x = NC (p)
-    auto nbr_m = [&](const float (&x)[NC], float edge) {
-        float m = __shfl_up_sync(FULL, x[NC - 1], 1, LX);
-        return xl == 0 ? edge : m;
-    };
-    auto nbr_p = [&](const float (&x)[NC], float edge) {
-        float p = __shfl_down_sync(FULL, x[0], 1, LX);
-        return xl == LX - 1 ? edge : p;
-    };
+    const float s_in[3] = {sc.in[0], sc.in[1], sc.in[2]};
 
-    // rows of level kk carried from the previous step (loaded there as level kk+1)
-    float u0[NC], v0[NC], vs[NC], w0[NC];
-    // level kk-1 at the cell, and the lower vertical pair sums of level kk
-    float ud[NC], vd[NC], wd[NC], pzu[NC], pzv[NC], pzw[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        ud[c] = vd[c] = wd[c] = pzu[c] = pzv[c] = pzw[c] = 0.f;
-        u0[c] = v0[c] = vs[c] = w0[c] = 0.f;
-    }
+    MarchRegs<NC> st;
+    st.zero();
     int waited = 0;   // planes 0..waited-1 are known complete
+    int lp = 0;       // plane index of the level being marched
+
+    // the staged planes of level kk (up = 0) and kk+1 (up = 1)
+    auto rowld = [&](int f, int up, int dr, float (&o)[NC]) {
+        ld(stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + c0, o, s_in[f]);
+    };
+    auto edgeld = [&](int f, int up, int dr) {
+        return ld1(stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + ce, s_in[f]);
+    };
 
     // One level of the march.  Returns false on abort.
     auto level = [&](const int kk) -> bool {
-        const int lp = kk - pb;
+        lp = kk - pb;
         bool ok = true;
         if (lp == 0) ok = mbar_wait_bounded(&bars[slot(0)], parity(0), kWaitLimitNs);
         const bool have_up = (kk + 1 <= pe);
@@ -375,120 +554,9 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC>& sm
         if (!ok) *abort_flag = 1;
         if (ok) {
             waited = lp + (have_up ? 2 : 1);
-            const T* P = stages + slot(lp) * L::STAGE;   // level kk
-            if (lp == 0) {
-                ld(P + FU + r * BW + c0, u0, su_in);
-                ld(P + FV + r * BW + c0, v0, sv_in);
-                ld(P + FV + (r - 1) * BW + c0, vs, sv_in);
-                ld(P + FW + r * BW + c0, w0, sw_in);
-            }
-            float wn[NC];
-            ld(P + FW + (r + 1) * BW + c0, wn, sw_in);
-            const float ew = ld1(P + FW + r * BW + ce, sw_in);
-            float W[NC + 2];   // x = -1..NC
-            W[0] = nbr_m(w0, ew);
-            W[NC + 1] = nbr_p(w0, ew);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) W[c + 1] = w0[c];
-
-            // level kk+1 rows (upper terms; carried into the next step)
-            float uu[NC], vu[NC], vus[NC], wu[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) uu[c] = vu[c] = vus[c] = wu[c] = 0.f;
-            float euu = 0.f;
-            if (have_up) {
-                const T* Q = stages + slot(lp + 1) * L::STAGE;
-                ld(Q + FU + r * BW + c0, uu, su_in);
-                ld(Q + FV + r * BW + c0, vu, sv_in);
-                ld(Q + FV + (r - 1) * BW + c0, vus, sv_in);
-                ld(Q + FW + r * BW + c0, wu, sw_in);
-                euu = ld1(Q + FU + r * BW + ce, su_in);
-            }
-            // upper vertical pair sums of level kk = lower ones of level kk+1
-            float pzu_n[NC], pzv_n[NC], pzw_n[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                pzu_n[c] = W[c + 1] + W[c + 2];   // w(k,i) + w(k,i+1)
-                pzv_n[c] = w0[c] + wn[c];         // w(k,j) + w(k,j+1)
-                pzw_n[c] = w0[c] + wu[c];         // w(k) + w(k+1)
-            }
-
-            const bool compute = (kk >= kb) && (kk >= 2);
-            float ru[NC], rv[NC], rw[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ru[c] = rv[c] = rw[c] = 0.f;
-            if (compute) {
-                float us[NC], un[NC], vn[NC], ws[NC];
-                ld(P + FU + (r - 1) * BW + c0, us, su_in);
-                ld(P + FU + (r + 1) * BW + c0, un, su_in);
-                ld(P + FV + (r + 1) * BW + c0, vn, sv_in);
-                ld(P + FW + (r - 1) * BW + c0, ws, sw_in);
-                const float eu = ld1(P + FU + r * BW + ce, su_in);
-                const float ev = ld1(P + FV + r * BW + ce, sv_in);
-                const float eun = ld1(P + FU + (r + 1) * BW + ce, su_in);
-                const float evs = ld1(P + FV + (r - 1) * BW + ce, sv_in);
-                float U[NC + 2], V[NC + 2];   // x = -1..NC
-                float UN[NC + 1], UU[NC + 1];  // x = -1..NC-1
-                float VS[NC + 1];              // x = 0..NC
-                U[0] = nbr_m(u0, eu);
-                U[NC + 1] = nbr_p(u0, eu);
-                V[0] = nbr_m(v0, ev);
-                V[NC + 1] = nbr_p(v0, ev);
-                UN[0] = nbr_m(un, eun);
-                UU[0] = nbr_m(uu, euu);
-                VS[NC] = nbr_p(vs, evs);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    U[c + 1] = u0[c];
-                    V[c + 1] = v0[c];
-                    UN[c + 1] = un[c];
-                    UU[c + 1] = uu[c];
-                    VS[c] = vs[c];
-                }
-
-                // pair sums along x shared by neighbouring cells: index c is the
-                // pair (x = c-1, c)
-                float pxu[NC + 1], qx[NC + 1], rx[NC + 1], pxv[NC], pys[NC];
-#pragma unroll
-                for (int c = 0; c < NC + 1; ++c) {
-                    pxu[c] = U[c] + U[c + 1];     // u(i-1) + u(i)
-                    qx[c] = U[c] + UN[c];         // u(j,i-1) + u(j+1,i-1)
-                    rx[c] = U[c] + UU[c];         // u(k,i-1) + u(k+1,i-1)
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    pxv[c] = V[c + 1] + V[c + 2];  // v(j,i) + v(j,i+1)
-                    pys[c] = VS[c] + VS[c + 1];    // v(j-1,i) + v(j-1,i+1)
-                }
-                const float tz1 = __ldg(cf.tz + kk);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    // su
-                    float x = tcx * fmaf(-U[c + 2], pxu[c + 1], U[c] * pxu[c]);
-                    x = fmaf(tcy, fmaf(-un[c], pxv[c], us[c] * pys[c]), x);
-                    ru[c] = fmaf(tz1, ud[c] * pzu[c], x);
-                    // sv
-                    float y = tcx * fmaf(-V[c + 2], qx[c + 1], V[c] * qx[c]);
-                    y = fmaf(tcy, fmaf(-vn[c], V[c + 1] + vn[c], vs[c] * (V[c + 1] + vs[c])), y);
-                    rv[c] = fmaf(tz1, vd[c] * pzv[c], y);
-                }
-                if (have_up) {   // kk < nz: upper vertical fluxes and sw
-                    const float tz2 = __ldg(cf.tz + nzp2 + kk);
-                    const float td1 = __ldg(cf.tz + 2 * nzp2 + kk);
-                    const float td2 = __ldg(cf.tz + 3 * nzp2 + kk);
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        ru[c] = fmaf(-tz2, uu[c] * pzu_n[c], ru[c]);
-                        rv[c] = fmaf(-tz2, vu[c] * pzv_n[c], rv[c]);
-                        float z = tcx * fmaf(-W[c + 2], rx[c + 1], W[c] * rx[c]);
-                        z = fmaf(tcy, fmaf(-wn[c], V[c + 1] + vu[c], ws[c] * (vs[c] + vus[c])), z);
-                        z = fmaf(td1, wd[c] * pzw[c], z);
-                        rw[c] = fmaf(-td2, wu[c] * pzw_n[c], z);
-                    }
-                }
-            }
-
-            if (kk >= kb && valid) {
+            auto out = [&](const float (&ru)[NC], const float (&rv)[NC], const float (&rw)[NC],
+                           const float (&u0)[NC], const float (&v0)[NC], const float (&w0)[NC]) {
+                if (!(kk >= kb && valid)) return;
                 float a[NC], b[NC], d[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -509,22 +577,9 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC>& sm
                 }
                 Epilogue<T, MODE>::template storevec<NC>(o0, o1, o2, row_off + (long long)kk * g.pk, a, b, d, g, j,
                                                          i0);
-            }
-
-            // roll: level kk becomes level k-1, level kk+1 becomes level kk
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                ud[c] = u0[c];
-                vd[c] = v0[c];
-                wd[c] = w0[c];
-                pzu[c] = pzu_n[c];
-                pzv[c] = pzv_n[c];
-                pzw[c] = pzw_n[c];
-                u0[c] = uu[c];
-                v0[c] = vu[c];
-                vs[c] = vus[c];
-                w0[c] = wu[c];
-            }
+            };
+            march_level<NC, LX>(st, rowld, edgeld, out, xl, lp == 0, have_up, (kk >= kb) && (kk >= 2), tcx, tcy,
+                                cf.tz, kk, nzp2);
         }
         __syncthreads();
         if (*abort_flag) return false;

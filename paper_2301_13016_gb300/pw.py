@@ -53,6 +53,7 @@ SIGNATURES = [
     ("pw_destroy", ctypes.c_int, [_VP]),
     ("pw_set_kernel", ctypes.c_int, [_VP, _I32]),
     ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
+    ("pw_set_step_blocking", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
@@ -235,6 +236,13 @@ class PW:
     def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0, cells=0):
         _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg)),
                "pw_set_tma_config")
+
+    def set_step_blocking(self, steps_per_pass=0, ty=0, stages=0, ctas_per_sm=0, nseg=0):
+        """Temporal blocking of step(): 1 or 2 steps per kernel pass (0 =
+        automatic = 1; 2 needs the TMA path and a halo >= 2), and the
+        two-step kernel's launch shape (0 = automatic)."""
+        _check(lib().pw_set_step_blocking(self.h, int(steps_per_pass), int(ty), int(stages), int(ctas_per_sm),
+                                          int(nseg)), "pw_set_step_blocking")
 
     @property
     def last_kernel(self):
