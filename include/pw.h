@@ -122,15 +122,20 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
  * Launch shape of the TMA k-march kernel: lanes_x = lanes per row, cells =
  * consecutive cells per thread along x (tile width lanes_x * cells columns),
  * ty = rows per CTA, stages = planes buffered per CTA, nseg = CTAs along z
- * (0 = chosen from the grid and SM count).  Any argument 0 keeps the
- * automatic choice: (32, 4, 4, 4) for FP32, (16, 8, 4, 4) for 16-bit storage
- * when nx is a multiple of 8.  Instantiated (lanes_x, ty, stages, cells):
- * (32,4,4,4) (32,8,3,4) (32,8,4,4) (32,8,6,4) (32,16,3,4) (16,4,4,4)
- * (16,8,4,4), and for 16-bit storage also (16,4,4,8) (16,8,4,8); others, and
- * cells = 8 with nx not a multiple of 8, give PW_ERR_UNSUPPORTED.
+ * (0 = chosen from the grid and SM count), rows_per_thread = 1, or 2 (a
+ * thread computes each cell together with the cell one row further on, in
+ * packed FP32x2 arithmetic; same results bit for bit).  Any argument 0 keeps
+ * the automatic choice, (lanes_x, ty, stages, cells, rows_per_thread) =
+ * (32, 4, 4, 4, 1) for FP32 and (16, 8, 4, 8, 1) for 16-bit storage when nx
+ * is a multiple of 8 (else (32, 4, 4, 4, 1)).  Instantiated (lanes_x, ty,
+ * stages, cells, rows_per_thread): (32,4,4,4,1) (32,8,3,4,1) (32,8,4,4,1)
+ * (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1) (16,8,4,4,1), and for 16-bit
+ * storage also (16,4,4,8,1) (16,8,4,8,1) (32,8,4,4,2) (32,16,4,4,2)
+ * (16,8,4,4,2); others, and cells = 8 with nx not a multiple of 8, give
+ * PW_ERR_UNSUPPORTED.
  */
 pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
-                              int32_t nseg);
+                              int32_t nseg, int32_t rows_per_thread);
 
 /*
  * Temporal blocking of pw_step.  steps_per_pass: 1 = one step per kernel

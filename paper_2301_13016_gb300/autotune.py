@@ -18,9 +18,10 @@ import torch
 
 BATCH_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=4, ctas_per_sm=c)
                     for lx, ty in ((32, 4), (32, 8), (16, 4), (16, 8)) for c in (0, 2)]
-GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns, cells=nc)
-                   for lx, ty, st, nc in ((32, 4, 4, 4), (32, 8, 4, 4), (32, 8, 6, 4), (16, 4, 4, 4), (16, 8, 4, 4),
-                                          (16, 4, 4, 8), (16, 8, 4, 8))
+GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns, cells=nc, rows=rp)
+                   for lx, ty, st, nc, rp in ((32, 4, 4, 4, 1), (32, 8, 4, 4, 1), (32, 8, 6, 4, 1), (16, 4, 4, 4, 1),
+                                              (16, 8, 4, 4, 1), (16, 4, 4, 8, 1), (16, 8, 4, 8, 1), (32, 8, 4, 4, 2),
+                                              (32, 16, 4, 4, 2), (16, 8, 4, 4, 2))
                    for ns in (0, 1, 2, 4)]
 
 
@@ -147,7 +148,9 @@ def main(argv=None):
     p.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--tag", default="")
+    p.add_argument("--only", default="", help="one shape LANES,TY,STAGES,CELLS[,ROWS] (e.g. 16,8,4,8)")
     a = p.parse_args(argv)
+    only = tuple(int(x) for x in a.only.split(",")) if a.only else None
     c = inputs.make_coeffs(a.nz)
     g = pwlib.Grid(a.nx, a.ny, a.nz, dtype=a.dtype)
     h = pwlib.PW(g, c)
@@ -161,18 +164,19 @@ def main(argv=None):
     res = {}
     seen = set()
     for cand in GRID_CANDIDATES:
-        key = (cand["lanes_x"], cand["ty"], cand["stages"], cand["cells"])
-        if key in seen:
+        key = (cand["lanes_x"], cand["ty"], cand["stages"], cand["cells"], cand["rows"])
+        if key in seen or (only and key[:len(only)] != only):
             continue
         seen.add(key)
         try:
-            h.set_tma_config(cand["ty"], cand["stages"], 0, lanes_x=cand["lanes_x"], cells=cand["cells"])
+            h.set_tma_config(cand["ty"], cand["stages"], 0, lanes_x=cand["lanes_x"], cells=cand["cells"],
+                             rows=cand["rows"])
         except RuntimeError:
             continue
         ms_t = _time(lambda: h.tendencies(*dev, *outs, scale=sc, stream=stream), 3, a.reps, stream)
         ms_s = _time(lambda: h.step(*dev, *tmp, 0.0, 2, scale=sc[:3], stream=stream), 2, a.reps, stream) / 2
         h.sync(stream)
-        res[f"lanes{key[0]}_ty{key[1]}_s{key[2]}_c{key[3]}"] = {"tend_gcells": g.cells / ms_t / 1e6,
+        res[f"lanes{key[0]}_ty{key[1]}_s{key[2]}_c{key[3]}_r{key[4]}"] = {"tend_gcells": g.cells / ms_t / 1e6,
                                                       "step_gcells": g.cells / ms_s / 1e6}
     print(json.dumps({"grid": [a.nx, a.ny, a.nz], "dtype": a.dtype, "tag": a.tag, "device": _device_key(),
                       "shapes": res}), flush=True)

@@ -204,9 +204,10 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
     return PW_OK;
 }
 
-// Launch shape of the TMA kernel: user overrides, else ty = 4 rows, 4 stages
-// (the fastest measured shape on GB300 for FP32 and 16-bit storage), and
-// enough k segments for about two waves of CTAs over the SMs.
+// Launch shape of the TMA kernel: user overrides, else 32 lanes x 4 cells x
+// 4 rows for FP32 and 16 lanes x 8 cells x 8 rows for 16-bit storage (nx a
+// multiple of 8), 4 stages (the fastest measured shapes on GB300), and enough
+// k segments for about two waves of CTAs over the SMs.
 static TmaConfig choose_tma(pw_handle_t h) {
     if (h->tma_auto.ty) return h->tma_auto;
     TmaConfig c;
@@ -214,7 +215,8 @@ static TmaConfig choose_tma(pw_handle_t h) {
     const bool wide = dtype_size(h->grid.dtype) == 2 && h->grid.nx % 8 == 0;
     c.lx = h->tma_user.lx ? h->tma_user.lx : (wide ? 16 : 32);
     c.nc = h->tma_user.nc ? h->tma_user.nc : (wide ? 8 : 4);
-    c.ty = h->tma_user.ty ? h->tma_user.ty : 4;
+    c.ty = h->tma_user.ty ? h->tma_user.ty : (wide ? 8 : 4);
+    c.rp = h->tma_user.rp ? h->tma_user.rp : 1;
     c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
     if (h->tma_user.nseg) {
         c.nseg = h->tma_user.nseg;
@@ -365,17 +367,21 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind) {
 }
 
 pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
-                              int32_t nseg) {
+                              int32_t nseg, int32_t rows_per_thread) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
+    if (rows_per_thread < 0 || rows_per_thread > 2) return fail(PW_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
     TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
     c.nc = cells ? cells : 4;
+    c.rp = rows_per_thread ? rows_per_thread : 1;
     if (!tma_config_supported(h->grid.dtype, c))
-        return fail(PW_ERR_UNSUPPORTED, "no TMA kernel instance for lanes_x=%d cells=%d ty=%d stages=%d (dtype %d)",
-                    c.lx, c.nc, c.ty, c.stages, (int)h->grid.dtype);
+        return fail(PW_ERR_UNSUPPORTED,
+                    "no TMA kernel instance for lanes_x=%d cells=%d ty=%d stages=%d rows_per_thread=%d (dtype %d)",
+                    c.lx, c.nc, c.ty, c.stages, c.rp, (int)h->grid.dtype);
     if (h->grid.nx % c.nc) return fail(PW_ERR_UNSUPPORTED, "cells=%d needs nx to be a multiple of %d", c.nc, c.nc);
     h->tma_user = TmaConfig{lanes_x, ty, stages, nseg};
     h->tma_user.nc = cells;
+    h->tma_user.rp = rows_per_thread;
     h->tma_auto = TmaConfig{0, 0, 0, 0};
     for (auto& m : h->maps) m.ptr = nullptr;
     return PW_OK;
@@ -660,6 +666,9 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
             }
             e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);
             done += 1;
+            // the single-step k-march writes the images of a one-cell halo only
+            for (int q = 0; q < 3 && e == cudaSuccess && g.halo != 1; ++q)
+                e = launch_fill_halo(dtp, g, dst[q], h->num_sms, s);
         } else {
             e = launch_step_generic(dtp, g, src[0], src[1], src[2], dst[0], dst[1], dst[2], sc, scaled, cf, dt,
                                     h->num_sms, s);

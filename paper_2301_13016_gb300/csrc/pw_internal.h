@@ -39,6 +39,7 @@ struct TmaConfig {
     int nc = 4;         // cells per thread along x (8: 16-bit storage only)
     int seg0 = 0;       // first segment to launch
     int seg_count = 0;  // segments to launch (0 = all nseg)
+    int rp = 1;         // rows per thread: 1, or 2 (packed FP32x2 arithmetic on row pairs)
 };
 
 // Launch shape of the two-step (temporal blocking) k-march kernel.

@@ -223,8 +223,11 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                         d[c] *= sc.out[2];
                     }
                 }
-                Epilogue<T, MODE_STEP>::template storevec<NC>(o0, o1, o2, row_off + (long long)m * g.pk, a, b, d, g,
-                                                              j, i0);
+                const long long o = row_off + (long long)m * g.pk;
+                storev<NC>(o0 + o, a);
+                storev<NC>(o1 + o, b);
+                storev<NC>(o2 + o, d);
+                StepImages::vec<T, NC>(o0, o1, o2, o, a, b, d, g, j, i0);
             };
             march_level<NC, 32>(st2, rowld2, edgeld2, out2, lane, m == kb1, m + 1 <= ke1, (m >= kb) && (m >= 2),
                                 tcx, tcy, cf.tz, m, nzp2);

@@ -52,7 +52,7 @@ SIGNATURES = [
     ("pw_create", ctypes.c_int, [ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t), ctypes.POINTER(_VP)]),
     ("pw_destroy", ctypes.c_int, [_VP]),
     ("pw_set_kernel", ctypes.c_int, [_VP, _I32]),
-    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
+    ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
     ("pw_set_step_blocking", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
@@ -233,9 +233,11 @@ class PW:
     def set_kernel(self, kind):
         _check(lib().pw_set_kernel(self.h, int(kind)), "pw_set_kernel")
 
-    def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0, cells=0):
-        _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg)),
-               "pw_set_tma_config")
+    def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0, cells=0, rows=0):
+        """Launch shape of the k-march kernel (0 = automatic); rows = rows per
+        thread (2: packed FP32x2 arithmetic on row pairs, 16-bit storage)."""
+        _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg),
+                                       int(rows)), "pw_set_tma_config")
 
     def set_step_blocking(self, steps_per_pass=0, ty=0, stages=0, ctas_per_sm=0, nseg=0):
         """Temporal blocking of step(): 1 or 2 steps per kernel pass (0 =

@@ -127,3 +127,42 @@ def test_eight_cells_per_thread(dtype, ty, nseg):
         assert np.all(np.abs(interior(x) - interior(y)) <= 2 * us * np.abs(interior(r)) + 2.0 ** -18 * interior(at) + 2 * floor)
     with pytest.raises(pwlib.PwError):
         pwlib.PW(pwlib.Grid(132, 8, 4, dtype=dtype), inputs.make_coeffs(4)).set_tma_config(4, 4, 0, lanes_x=16, cells=8)
+
+
+PAIRED = [(32, 8, 4, 4, 2), (32, 16, 4, 4, 2), (16, 8, 4, 4, 2)]
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("cfg", PAIRED, ids=["x".join(map(str, p)) for p in PAIRED])
+def test_two_rows_per_thread_bitwise(dtype, cfg):
+    """Two rows per thread (packed FP32x2 arithmetic on row pairs) gives the
+    same bits as one row per thread, for the source terms and for fused steps,
+    on tiles ragged in x (264 = 2 x 128 + 8 columns) and in y (13 rows: the
+    last row pair has its second row outside the grid)."""
+    nx, ny, nz = 264, 13, 10
+    c = inputs.make_coeffs(nz)
+    f = inputs.random_fields(nx, ny, nz)
+    sc = precision.suggest_scales([float(x.abs().max()) for x in f], c, dtype)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    lx, ty, st, cells, rows = cfg
+    res = {}
+    for key, shape in (("one", (32, 4, 4, 4, 1)), ("two", cfg)):
+        h = pwlib.PW(g, c)
+        h.set_tma_config(shape[1], shape[2], 0, lanes_x=shape[0], cells=shape[3], rows=shape[4])
+        dev = [g.from_dense(x, scale=s) for x, s in zip(f, sc[:3])]
+        outs = [g.alloc(fill=NAN) for _ in range(3)]
+        h.tendencies(*dev, *outs, scale=sc)
+        tmp = [g.alloc(fill=NAN) for _ in range(3)]
+        h.step(*dev, *tmp, 0.5, 3, scale=sc[:3])
+        h.sync()
+        assert h.last_kernel == 2
+        res[key] = [g.view(t).contiguous().view(torch.int16) for t in outs + dev]
+    for a, b in zip(res["one"], res["two"]):
+        assert torch.equal(a, b)
+
+
+def test_two_rows_per_thread_needs_16bit_storage():
+    g = pwlib.Grid(128, 8, 4)
+    with pytest.raises(pwlib.PwError) as e:
+        pwlib.PW(g, inputs.make_coeffs(4)).set_tma_config(8, 4, 0, lanes_x=32, cells=4, rows=2)
+    assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
