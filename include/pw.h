@@ -138,6 +138,13 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
                               int32_t nseg, int32_t rows_per_thread);
 
 /*
+ * The launch shape the TMA k-march kernel will use on this handle (the
+ * automatic choice, or what pw_set_tma_config fixed): out = {lanes_x, cells,
+ * ty, stages, nseg, rows_per_thread}.
+ */
+pw_status_t pw_get_tma_config(pw_handle_t h, int32_t out[6]);
+
+/*
  * Temporal blocking of pw_step.  steps_per_pass: 1 = one step per kernel
  * pass; 2 = two steps per pass (needs the TMA path, a lateral halo >= 2 and
  * interior rows starting >= 7 elements into their padded row, else pw_step

@@ -75,7 +75,9 @@ struct pw_handle_s {
     int* d_err = nullptr;       // device status word (bounded-wait timeouts)
     int kernel_kind = 0;        // 0 auto, 1 generic, 2 TMA
     int last_kernel = 0;
-    TmaConfig tma_user{0, 0, 0, 0};
+    // user overrides: every field 0 = automatic (nc and rp too, whose struct
+    // defaults are the values a launch uses)
+    TmaConfig tma_user{0, 0, 0, 0, 0, 0, 0, 0};
     TmaConfig tma_auto{0, 0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
     int steps_per_pass = 0;           // pw_step temporal blocking: 0 auto (= 1), 1, 2
     Step2Config step2_user{0, 0, 0, 0};
@@ -424,6 +426,18 @@ static Step2Config choose_step2(pw_handle_t h) {
     if (c.nseg > h->grid.nz / 2) c.nseg = std::max(1, h->grid.nz / 2);
     h->step2_auto = c;
     return c;
+}
+
+pw_status_t pw_get_tma_config(pw_handle_t h, int32_t out[6]) {
+    if (!h || !out) return fail(PW_ERR_ARG, "handle or out is NULL");
+    const TmaConfig c = choose_tma(h);
+    out[0] = c.lx;
+    out[1] = c.nc;
+    out[2] = c.ty;
+    out[3] = c.stages;
+    out[4] = c.nseg;
+    out[5] = c.rp;
+    return PW_OK;
 }
 
 int32_t pw_last_kernel(pw_handle_t h) { return h ? h->last_kernel : 0; }
