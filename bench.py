@@ -596,6 +596,7 @@ def form_adjoint(args):
     adj = lambda: h.adjoint(*qs, *gs, *g2, alpha=dt, flags=pwlib.PW_ADJ_PERIODIC | pwlib.PW_ADJ_ADD_LAMBDA,
                             stream=stream)
     adj()
+    adj_kernel = {1: "adjoint_gather_kernel", 2: "adjoint_tma_kernel"}.get(h.last_kernel, "none")
     adj_ms = _events_ms(adj, 20, stream)
     cell_steps = g.cells * nsteps
     peak, kind = measured_peak()
@@ -608,7 +609,7 @@ def form_adjoint(args):
                 "backward_gcell_steps": cell_steps / (bwd_ms / 1e3) / 1e9,
                 "adjoint_kernel_ms": adj_ms, "adjoint_kernel_gcells": g.cells / (adj_ms / 1e3) / 1e9,
                 "vs_fp32_form": (g.cells / (adj_ms / 1e3) / 1e9) / ref, "fp32_form_gcells": ref,
-                "roofline": {"bound": "hbm", "kernel": "adjoint_gather_kernel", "achieved": adj_gbs, "peak": peak,
+                "roofline": {"bound": "hbm", "kernel": adj_kernel, "achieved": adj_gbs, "peak": peak,
                              "unit": "GB/s", "frac": adj_gbs / peak, "peak_kind": kind, "bytes_per_cell": 36}})
 
 
