@@ -50,6 +50,10 @@ def parse():
     p.add_argument("--workload", choices=["2048", "512"], default="2048")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-grids", type=int, default=512, help="batch form: number of grids")
+    p.add_argument("--batch-tile", default="", help="batch form: LANES,TY,STAGES,CTAS_PER_SM (skips the autotuner)")
+    p.add_argument("--skip-fp32-ref", action="store_true",
+                   help="forms: do not time the FP32 tendency form beside them (small profiling runs)")
     p.add_argument("--form", choices=FORMS, default="tend",
                    help="tend (default: the headline FP32 tendency benchmark) or another form of the path")
     return p.parse_args()
@@ -511,8 +515,8 @@ def form_batch(args):
     import paper_2301_13016_gb300 as pwlib
     from paper_2301_13016_gb300 import autotune, inputs
     stream = torch.cuda.current_stream()
-    ref = _fp32_reference_rate(2048, 2048, 64, 50, stream)
-    shapes = inputs.batch_shapes()
+    ref = None if args.skip_fp32_ref else _fp32_reference_rate(2048, 2048, 64, 50, stream)
+    shapes = inputs.batch_shapes(n=args.batch_grids)
     grids, coeffs, dev, outs = [], [], [], []
     for q, (nx, ny, nz) in enumerate(shapes):
         g = pwlib.Grid(nx, ny, nz)
@@ -527,9 +531,14 @@ def form_batch(args):
     flds = ([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev],
             [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
     t0 = time.perf_counter()
-    cfg, times = autotune.tune_batch(b, flds, reps=3, force=True,
-                                     cache_path=os.path.join(ROOT, "gpurun_out", "tune_batch.json")
-                                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    if args.batch_tile:
+        lx, ty, st, cps = (int(x) for x in args.batch_tile.split(","))
+        cfg, times = dict(lanes_x=lx, ty=ty, stages=st, ctas_per_sm=cps), {}
+        b.set_config(**cfg)
+    else:
+        cfg, times = autotune.tune_batch(b, flds, reps=3, force=True,
+                                         cache_path=os.path.join(ROOT, "gpurun_out", "tune_batch.json")
+                                         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
     tune_s = time.perf_counter() - t0
     f = lambda: b.tendencies(*flds, stream=stream)
     for _ in range(args.warmup):
@@ -540,11 +549,12 @@ def form_batch(args):
     val = info["cells"] / (ms / 1e3) / 1e9
     peak, kind = measured_peak()
     achieved = 24 * info["cells"] / (ms / 1e3) / 1e9
-    _form_line(args, "batch", "PW tendencies Gcell/s, 512 independent grids in one persistent graph-replayed launch",
-               val, "Gcell/s", {"workload": "512 grids, nx, ny ~ U{32..384 step 4}, nz ~ U{32..128} (seed 2304), "
+    n = args.batch_grids
+    _form_line(args, "batch", f"PW tendencies Gcell/s, {n} independent grids in one persistent graph-replayed launch",
+               val, "Gcell/s", {"workload": f"{n} grids, nx, ny ~ U{{32..384 step 4}}, nz ~ U{{32..128}} (seed 2304), "
                                             "FP32, random 10*N(0,1)", "cells": info["cells"],
                                 "items": info["items"], "ctas": info["ctas"], "tile": cfg},
-               {"dtype": "f32", "ms_per_step": ms, "vs_fp32_form": val / ref, "fp32_form_gcells": ref,
+               {"dtype": "f32", "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
                 "autotune_s": tune_s, "autotune_ms": times,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": 24},
