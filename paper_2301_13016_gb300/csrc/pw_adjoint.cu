@@ -274,11 +274,19 @@ __global__ void __launch_bounds__(32 * TY)
                 auto Up = [&](int dj, int di) { return A(Pp, 0, dj, di); };
                 auto Vp = [&](int dj, int di) { return A(Pp, 1, dj, di); };
                 auto Wp = [&](int dj, int di) { return A(Pp, 2, dj, di); };
-                auto LU0 = [&](int dj, int di) { return lu0 ? A(P0, 3, dj, di) : 0.f; };
-                auto LV0 = [&](int dj, int di) { return lu0 ? A(P0, 4, dj, di) : 0.f; };
-                auto LW0 = [&](int dj, int di) { return lw0 ? A(P0, 5, dj, di) : 0.f; };
-                auto LUT0 = [&](int dj, int di) { return lut0 ? A(P0, 3, dj, di) : 0.f; };
-                auto LVT0 = [&](int dj, int di) { return lut0 ? A(P0, 4, dj, di) : 0.f; };
+                // Every shared-memory read below is in bounds (all ring slots exist),
+                // so terms that do not apply at this level are computed anyway and
+                // dropped by a select: no branch stands between the loads, which lets
+                // them issue together.  A dropped term may have read a slot that holds
+                // another level (or is being refilled): the select discards it, so
+                // nothing from it reaches the sums, NaN included.
+                auto keep = [](bool c, float t) { return c ? t : 0.f; };
+                auto LU0 = [&](int dj, int di) { return keep(lu0, A(P0, 3, dj, di)); };
+                auto LV0 = [&](int dj, int di) { return keep(lu0, A(P0, 4, dj, di)); };
+                auto LW0 = [&](int dj, int di) { return keep(lw0, A(P0, 5, dj, di)); };
+                auto LUT0 = [&](int dj, int di) { return keep(lut0, A(P0, 3, dj, di)); };
+                auto LVT0 = [&](int dj, int di) { return keep(lut0, A(P0, 4, dj, di)); };
+                const bool pu = has_p && lup, mu = has_m && lutm, mw = has_m && lwm, pw = has_p && lwp;
 
                 // two accumulators per gradient halve the dependent FMA chains
                 float ru = 0.f, rv = 0.f, rw = 0.f, ru2 = 0.f, rv2 = 0.f, rw2 = 0.f;
@@ -289,18 +297,16 @@ __global__ void __launch_bounds__(32 * TY)
                 ru2 -= tcx * LU0(0, 0) * U0(0, 1);
                 ru += tcy * LU0(1, 0) * (V0(0, 0) + V0(0, 1));
                 ru2 -= tcy * LU0(-1, 0) * (V0(-1, 0) + V0(-1, 1));
-                if (has_p && lup) ru += c1p * A(Pp, 3, 0, 0) * (W0(0, 0) + W0(0, 1));
-                if (has_m && lutm) ru2 -= c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1));
+                ru += keep(pu, c1p * A(Pp, 3, 0, 0) * (W0(0, 0) + W0(0, 1)));
+                ru2 -= keep(mu, c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1)));
                 ru += tcx * LV0(0, 1) * V0(0, 0);
                 ru2 += tcx * LV0(-1, 1) * V0(-1, 0);
                 ru -= tcx * LV0(0, 0) * V0(0, 1);
                 ru2 -= tcx * LV0(-1, 0) * V0(-1, 1);
                 ru += tcx * LW0(0, 1) * W0(0, 0);
                 ru2 -= tcx * LW0(0, 0) * W0(0, 1);
-                if (has_m && lwm) {
-                    ru += tcx * A(Pm, 5, 0, 1) * Wm(0, 0);
-                    ru2 -= tcx * A(Pm, 5, 0, 0) * Wm(0, 1);
-                }
+                ru += keep(mw, tcx * A(Pm, 5, 0, 1) * Wm(0, 0));
+                ru2 -= keep(mw, tcx * A(Pm, 5, 0, 0) * Wm(0, 1));
                 // ---- gv
                 rv += tcy * LU0(1, 0) * U0(0, 0);
                 rv2 += tcy * LU0(1, -1) * U0(0, -1);
@@ -312,37 +318,29 @@ __global__ void __launch_bounds__(32 * TY)
                 rv2 += tcy * LV0(0, 0) * V0(-1, 0);
                 rv -= tcy * LV0(-1, 0) * (V0(-1, 0) + 2.f * V0(0, 0));
                 rv2 -= tcy * LV0(0, 0) * V0(1, 0);
-                if (has_p && lup) rv += c1p * A(Pp, 4, 0, 0) * (W0(0, 0) + W0(1, 0));
-                if (has_m && lutm) rv2 -= c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0));
+                rv += keep(pu, c1p * A(Pp, 4, 0, 0) * (W0(0, 0) + W0(1, 0)));
+                rv2 -= keep(mu, c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0)));
                 rv += tcy * LW0(1, 0) * W0(0, 0);
                 rv2 -= tcy * LW0(0, 0) * W0(1, 0);
-                if (has_m && lwm) {
-                    rv += tcy * A(Pm, 5, 1, 0) * Wm(0, 0);
-                    rv2 -= tcy * A(Pm, 5, 0, 0) * Wm(1, 0);
-                }
+                rv += keep(mw, tcy * A(Pm, 5, 1, 0) * Wm(0, 0));
+                rv2 -= keep(mw, tcy * A(Pm, 5, 0, 0) * Wm(1, 0));
                 // ---- gw
-                if (has_p) {
-                    if (lup) {
-                        rw += c1p * A(Pp, 3, 0, 0) * U0(0, 0);
-                        rw2 += c1p * A(Pp, 3, 0, -1) * U0(0, -1);
-                        rw += c1p * A(Pp, 4, 0, 0) * V0(0, 0);
-                        rw2 += c1p * A(Pp, 4, -1, 0) * V0(-1, 0);
-                    }
-                    rw -= c2 * LUT0(0, 0) * Up(0, 0);
-                    rw2 -= c2 * LUT0(0, -1) * Up(0, -1);
-                    rw -= c2 * LVT0(0, 0) * Vp(0, 0);
-                    rw2 -= c2 * LVT0(-1, 0) * Vp(-1, 0);
-                    rw += tcx * LW0(0, 1) * (U0(0, 0) + Up(0, 0));
-                    rw2 -= tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1));
-                    rw += tcy * LW0(1, 0) * (V0(0, 0) + Vp(0, 0));
-                    rw2 -= tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0));
-                    if (lwp) rw += d1p * A(Pp, 5, 0, 0) * (Wp(0, 0) + 2.f * W0(0, 0));
-                    rw2 -= d2 * LW0(0, 0) * Wp(0, 0);
-                }
-                if (has_m) {
-                    rw += d1 * LW0(0, 0) * Wm(0, 0);
-                    if (lwm) rw2 -= d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0));
-                }
+                rw += keep(pu, c1p * A(Pp, 3, 0, 0) * U0(0, 0));
+                rw2 += keep(pu, c1p * A(Pp, 3, 0, -1) * U0(0, -1));
+                rw += keep(pu, c1p * A(Pp, 4, 0, 0) * V0(0, 0));
+                rw2 += keep(pu, c1p * A(Pp, 4, -1, 0) * V0(-1, 0));
+                rw -= keep(has_p, c2 * LUT0(0, 0) * Up(0, 0));
+                rw2 -= keep(has_p, c2 * LUT0(0, -1) * Up(0, -1));
+                rw -= keep(has_p, c2 * LVT0(0, 0) * Vp(0, 0));
+                rw2 -= keep(has_p, c2 * LVT0(-1, 0) * Vp(-1, 0));
+                rw += keep(has_p, tcx * LW0(0, 1) * (U0(0, 0) + Up(0, 0)));
+                rw2 -= keep(has_p, tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1)));
+                rw += keep(has_p, tcy * LW0(1, 0) * (V0(0, 0) + Vp(0, 0)));
+                rw2 -= keep(has_p, tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0)));
+                rw += keep(pw, d1p * A(Pp, 5, 0, 0) * (Wp(0, 0) + 2.f * W0(0, 0)));
+                rw2 -= keep(has_p, d2 * LW0(0, 0) * Wp(0, 0));
+                rw += keep(has_m, d1 * LW0(0, 0) * Wm(0, 0));
+                rw2 -= keep(mw, d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0)));
                 ru += ru2;
                 rv += rv2;
                 rw += rw2;

