@@ -612,7 +612,7 @@ def form_adjoint(args):
     adj = lambda: h.adjoint(*qs, *gs, *g2, alpha=dt, flags=pwlib.PW_ADJ_PERIODIC | pwlib.PW_ADJ_ADD_LAMBDA,
                             stream=stream)
     adj()
-    adj_kernel = {1: "adjoint_gather_kernel", 2: "adjoint_tma_kernel"}.get(h.last_kernel, "none")
+    adj_kernel = {1: "adjoint_gather_kernel", 2: "adjoint_vec_kernel"}.get(h.last_kernel, "none")
     adj_ms = _events_ms(adj, 20, stream)
     cell_steps = g.cells * nsteps
     peak, kind = measured_peak()

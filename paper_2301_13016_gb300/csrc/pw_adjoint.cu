@@ -19,6 +19,8 @@
 // periodic domain, which equals the full-array result folded back onto the
 // interior; u, v, w must carry periodic halos).
 #include "pw_device.cuh"
+
+#include <type_traits>
 #include "pw_internal.h"
 
 namespace pw {
@@ -165,10 +167,8 @@ __global__ void adjoint_gather_kernel(const GridDev g, const AdjArgs a, const Co
 // TMA k-march adjoint (periodic mode, FP32).  A CTA owns 128 x TY interior
 // columns; one thread issues 3D TMA copies of the u, v, w and lsu, lsv, lsw
 // planes (tile plus one-cell halo) into a ring of S slots, keeping levels
-// k-1, k, k+1 resident while S-3 more are in flight.  Thread (lane, ty)
-// gathers 4 cells x = lane + 32q of row ty: every shared-memory access of a
-// warp touches 32 consecutive words (no bank conflicts, no shuffles).  The
-// halos of u, v, w and of l must hold periodic images.
+// k-1, k, k+1 resident while S-3 more are in flight.  The halos of u, v, w
+// and of l must hold periodic images.
 constexpr int kAdjTX = 128;
 constexpr int kAdjPAD = 4;                       // 16-byte granule of FP32
 constexpr int kAdjBW = kAdjTX + 2 * kAdjPAD;
@@ -187,9 +187,20 @@ struct AdjMaps {
     CUtensorMap m[6];   // u, v, w, lsu, lsv, lsw
 };
 
+// ---------------------------------------------------------------------------
+// The gather kernel on that ring: a thread owns 4 consecutive cells of one
+// row, so each (field, level, row) it needs is one 16-byte shared load for
+// all 4 cells, and the x neighbours come from the adjacent lanes by warp
+// shuffles (the row's end lanes read theirs from the halo columns), as in
+// the forward k-march: 30 vector loads per level.  (Four cells 32 columns
+// apart, read one word at a time, took about 200 scalar loads per level and
+// ran at 58 against 79 Gcell/s on GB300.)  Levels 3..nz-2 have every term and run without any masking; the
+// others select away the terms that do not exist there (a select, not a
+// multiplication by zero, so values read from a slot that holds another
+// level, or a sensitivity outside the scheme's outputs, never reach a sum).
 template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY)
-    adjoint_tma_kernel(const __grid_constant__ AdjMaps maps, float* __restrict__ gu, float* __restrict__ gv,
+__global__ void __launch_bounds__(32 * TY, 2)
+    adjoint_vec_kernel(const __grid_constant__ AdjMaps maps, float* __restrict__ gu, float* __restrict__ gv,
                        float* __restrict__ gw, const GridDev g, const int ox, const int nseg, const CoefDev cf,
                        const float alpha, const int accumulate, const int add_lambda, int* __restrict__ err) {
     using L = AdjLayout<TY, S>;
@@ -231,7 +242,14 @@ __global__ void __launch_bounds__(32 * TY)
     const float* tzd2 = cf.tz + 3 * nzp2;
     const float tcx = cf.tcx, tcy = cf.tcy;
     const int r = ty + 1;
+    const int c0 = kAdjPAD + 4 * lane;
+    // tile-edge neighbour column: lane 0 needs x = -1, lane 31 x = 128; the
+    // other lanes read lane 31's address (a broadcast)
+    const int ce = (lane == 0) ? kAdjPAD - 1 : kAdjPAD + kAdjTX;
     const int J = TY * blockIdx.y + 1 + ty;
+    const int I0 = 1 + kAdjTX * blockIdx.x + 4 * lane;
+    const bool valid = (J <= g.ny) && (I0 <= g.nx);
+    const unsigned FULL = 0xffffffffu;
     int waited = 0;
     bool aborted = false;
 
@@ -241,126 +259,190 @@ __global__ void __launch_bounds__(32 * TY)
         const int need_hi = (K + 1 <= pe) ? lp + 1 : lp;
         for (int p = (K == kb ? 0 : need_hi); p <= need_hi && ok; ++p)
             ok = mbar_wait_bounded(&bars[p % S], (uint32_t)((p / S) & 1), kWaitLimitNs);
-        ok = __all_sync(0xffffffffu, ok);
+        ok = __all_sync(FULL, ok);
         if (!ok) *abort_flag = 1;
         if (ok) {
             waited = need_hi + 1;
             const float* Pm = stages + ((lp - 1 + S) % S) * L::STAGE;   // level K-1 (valid when K-1 >= pb)
             const float* P0 = stages + (lp % S) * L::STAGE;             // level K
             const float* Pp = stages + ((lp + 1) % S) * L::STAGE;       // level K+1 (valid when K+1 <= pe)
+            // X[0..5] = the row at x = -1..4 relative to the thread's first cell
+            auto row = [&](const float* P, int f, int dj, float (&X)[6], bool lo, bool hi) {
+                const float* q = P + f * L::FIELD + (r + dj) * kAdjBW;
+                const float4 t = *reinterpret_cast<const float4*>(q + c0);
+                X[1] = t.x;
+                X[2] = t.y;
+                X[3] = t.z;
+                X[4] = t.w;
+                X[0] = X[5] = 0.f;
+                if (lo || hi) {
+                    const float e = q[ce];
+                    if (lo) {
+                        const float m = __shfl_up_sync(FULL, t.w, 1);
+                        X[0] = lane == 0 ? e : m;
+                    }
+                    if (hi) {
+                        const float pv = __shfl_down_sync(FULL, t.x, 1);
+                        X[5] = lane == 31 ? e : pv;
+                    }
+                }
+            };
+            // rows: [L]ambda or field, level (0: K, p: K+1, m: K-1), row (m, z, p: j-1, j, j+1)
+            float LU0m[6], LU0z[6], LU0p[6], LUpz[6], LUmz[6];
+            float LV0m[6], LV0z[6], LV0p[6], LVpz[6], LVpm[6], LVmz[6];
+            float LW0m[6], LW0z[6], LW0p[6], LWmz[6], LWmp[6], LWpz[6];
+            float U0z[6], U0p[6], Upz[6];
+            float V0m[6], V0z[6], V0p[6], Vpz[6], Vpm[6];
+            float W0z[6], W0p[6], Wmz[6], Wmp[6], Wpz[6];
+            row(P0, 3, -1, LU0m, false, false);
+            row(P0, 3, 0, LU0z, true, true);
+            row(P0, 3, 1, LU0p, true, false);
+            row(Pp, 3, 0, LUpz, true, false);
+            row(Pm, 3, 0, LUmz, false, false);
+            row(P0, 4, -1, LV0m, false, true);
+            row(P0, 4, 0, LV0z, true, true);
+            row(P0, 4, 1, LV0p, false, false);
+            row(Pp, 4, 0, LVpz, false, false);
+            row(Pp, 4, -1, LVpm, false, false);
+            row(Pm, 4, 0, LVmz, false, false);
+            row(P0, 5, -1, LW0m, false, false);
+            row(P0, 5, 0, LW0z, true, true);
+            row(P0, 5, 1, LW0p, false, false);
+            row(Pm, 5, 0, LWmz, false, true);
+            row(Pm, 5, 1, LWmp, false, false);
+            row(Pp, 5, 0, LWpz, false, false);
+            row(P0, 0, 0, U0z, true, true);
+            row(P0, 0, 1, U0p, true, false);
+            row(Pp, 0, 0, Upz, true, false);
+            row(P0, 1, -1, V0m, false, true);
+            row(P0, 1, 0, V0z, false, true);
+            row(P0, 1, 1, V0p, false, false);
+            row(Pp, 1, 0, Vpz, false, false);
+            row(Pp, 1, -1, Vpm, false, false);
+            row(P0, 2, 0, W0z, false, true);
+            row(P0, 2, 1, W0p, false, false);
+            row(Pm, 2, 0, Wmz, false, true);
+            row(Pm, 2, 1, Wmp, false, false);
+            row(Pp, 2, 0, Wpz, false, false);
+
             const bool has_m = (K - 1 >= 1), has_p = (K + 1 <= nz);
-            // sensitivities exist at output levels 2..nz (su, sv; upper terms
-            // 2..nz-1) and 2..nz-1 (sw)
-            const bool lu0 = (K >= 2), lum = (K - 1 >= 2), lup = (K + 1 <= nz);
-            const bool lut0 = (K >= 2 && K <= nz - 1), lutm = (K - 1 >= 2 && K - 1 <= nz - 1);
-            const bool lw0 = (K >= 2 && K <= nz - 1), lwm = (K - 1 >= 2 && K - 1 <= nz - 1),
-                       lwp = (K + 1 >= 2 && K + 1 <= nz - 1);
             const float c1p = has_p ? tzc1[K + 1] : 0.f, c2m = has_m ? tzc2[K - 1] : 0.f, c2 = tzc2[K];
             const float d1p = has_p ? tzd1[K + 1] : 0.f, d1 = tzd1[K], d2 = tzd2[K];
             const float d2m = has_m ? tzd2[K - 1] : 0.f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = lane + 32 * q;
-                const int c = x + kAdjPAD;
-                const int I = 1 + kAdjTX * blockIdx.x + x;
-                // field f at (level K+dk, row r+dj, column c+di)
-                auto A = [&](const float* P, int f, int dj, int di) { return P[f * L::FIELD + (r + dj) * kAdjBW + c + di]; };
-                auto U0 = [&](int dj, int di) { return A(P0, 0, dj, di); };
-                auto V0 = [&](int dj, int di) { return A(P0, 1, dj, di); };
-                auto W0 = [&](int dj, int di) { return A(P0, 2, dj, di); };
-                auto Um = [&](int dj, int di) { return A(Pm, 0, dj, di); };
-                auto Vm = [&](int dj, int di) { return A(Pm, 1, dj, di); };
-                auto Wm = [&](int dj, int di) { return A(Pm, 2, dj, di); };
-                auto Up = [&](int dj, int di) { return A(Pp, 0, dj, di); };
-                auto Vp = [&](int dj, int di) { return A(Pp, 1, dj, di); };
-                auto Wp = [&](int dj, int di) { return A(Pp, 2, dj, di); };
-                // Every shared-memory read below is in bounds (all ring slots exist),
-                // so terms that do not apply at this level are computed anyway and
-                // dropped by a select: no branch stands between the loads, which lets
-                // them issue together.  A dropped term may have read a slot that holds
-                // another level (or is being refilled): the select discards it, so
-                // nothing from it reaches the sums, NaN included.
-                auto keep = [](bool c, float t) { return c ? t : 0.f; };
-                auto LU0 = [&](int dj, int di) { return keep(lu0, A(P0, 3, dj, di)); };
-                auto LV0 = [&](int dj, int di) { return keep(lu0, A(P0, 4, dj, di)); };
-                auto LW0 = [&](int dj, int di) { return keep(lw0, A(P0, 5, dj, di)); };
-                auto LUT0 = [&](int dj, int di) { return keep(lut0, A(P0, 3, dj, di)); };
-                auto LVT0 = [&](int dj, int di) { return keep(lut0, A(P0, 4, dj, di)); };
+            float ru[4], rv[4], rw[4];
+
+            // the gather of one level; EDGE: levels where some terms do not exist
+            auto body = [&](auto edge_tag) {
+                constexpr bool EDGE = decltype(edge_tag)::value;
+                // sensitivities exist at output levels 2..nz (su, sv; upper terms
+                // 2..nz-1) and 2..nz-1 (sw)
+                const bool lu0 = (K >= 2), lw0 = (K >= 2 && K <= nz - 1);
+                const bool lutm = (K - 1 >= 2 && K - 1 <= nz - 1), lwm = lutm, lup = (K + 1 <= nz);
+                const bool lwp = (K + 1 >= 2 && K + 1 <= nz - 1);
                 const bool pu = has_p && lup, mu = has_m && lutm, mw = has_m && lwm, pw = has_p && lwp;
-
-                // two accumulators per gradient halve the dependent FMA chains
-                float ru = 0.f, rv = 0.f, rw = 0.f, ru2 = 0.f, rv2 = 0.f, rw2 = 0.f;
-                // ---- gu
-                ru += tcx * LU0(0, 1) * (U0(0, 1) + 2.f * U0(0, 0));
-                ru2 += tcx * LU0(0, 0) * U0(0, -1);
-                ru -= tcx * LU0(0, -1) * (U0(0, -1) + 2.f * U0(0, 0));
-                ru2 -= tcx * LU0(0, 0) * U0(0, 1);
-                ru += tcy * LU0(1, 0) * (V0(0, 0) + V0(0, 1));
-                ru2 -= tcy * LU0(-1, 0) * (V0(-1, 0) + V0(-1, 1));
-                ru += keep(pu, c1p * A(Pp, 3, 0, 0) * (W0(0, 0) + W0(0, 1)));
-                ru2 -= keep(mu, c2m * A(Pm, 3, 0, 0) * (Wm(0, 0) + Wm(0, 1)));
-                ru += tcx * LV0(0, 1) * V0(0, 0);
-                ru2 += tcx * LV0(-1, 1) * V0(-1, 0);
-                ru -= tcx * LV0(0, 0) * V0(0, 1);
-                ru2 -= tcx * LV0(-1, 0) * V0(-1, 1);
-                ru += tcx * LW0(0, 1) * W0(0, 0);
-                ru2 -= tcx * LW0(0, 0) * W0(0, 1);
-                ru += keep(mw, tcx * A(Pm, 5, 0, 1) * Wm(0, 0));
-                ru2 -= keep(mw, tcx * A(Pm, 5, 0, 0) * Wm(0, 1));
-                // ---- gv
-                rv += tcy * LU0(1, 0) * U0(0, 0);
-                rv2 += tcy * LU0(1, -1) * U0(0, -1);
-                rv -= tcy * LU0(0, 0) * U0(1, 0);
-                rv2 -= tcy * LU0(0, -1) * U0(1, -1);
-                rv += tcx * LV0(0, 1) * (U0(0, 0) + U0(1, 0));
-                rv2 -= tcx * LV0(0, -1) * (U0(0, -1) + U0(1, -1));
-                rv += tcy * LV0(1, 0) * (V0(1, 0) + 2.f * V0(0, 0));
-                rv2 += tcy * LV0(0, 0) * V0(-1, 0);
-                rv -= tcy * LV0(-1, 0) * (V0(-1, 0) + 2.f * V0(0, 0));
-                rv2 -= tcy * LV0(0, 0) * V0(1, 0);
-                rv += keep(pu, c1p * A(Pp, 4, 0, 0) * (W0(0, 0) + W0(1, 0)));
-                rv2 -= keep(mu, c2m * A(Pm, 4, 0, 0) * (Wm(0, 0) + Wm(1, 0)));
-                rv += tcy * LW0(1, 0) * W0(0, 0);
-                rv2 -= tcy * LW0(0, 0) * W0(1, 0);
-                rv += keep(mw, tcy * A(Pm, 5, 1, 0) * Wm(0, 0));
-                rv2 -= keep(mw, tcy * A(Pm, 5, 0, 0) * Wm(1, 0));
-                // ---- gw
-                rw += keep(pu, c1p * A(Pp, 3, 0, 0) * U0(0, 0));
-                rw2 += keep(pu, c1p * A(Pp, 3, 0, -1) * U0(0, -1));
-                rw += keep(pu, c1p * A(Pp, 4, 0, 0) * V0(0, 0));
-                rw2 += keep(pu, c1p * A(Pp, 4, -1, 0) * V0(-1, 0));
-                rw -= keep(has_p, c2 * LUT0(0, 0) * Up(0, 0));
-                rw2 -= keep(has_p, c2 * LUT0(0, -1) * Up(0, -1));
-                rw -= keep(has_p, c2 * LVT0(0, 0) * Vp(0, 0));
-                rw2 -= keep(has_p, c2 * LVT0(-1, 0) * Vp(-1, 0));
-                rw += keep(has_p, tcx * LW0(0, 1) * (U0(0, 0) + Up(0, 0)));
-                rw2 -= keep(has_p, tcx * LW0(0, -1) * (U0(0, -1) + Up(0, -1)));
-                rw += keep(has_p, tcy * LW0(1, 0) * (V0(0, 0) + Vp(0, 0)));
-                rw2 -= keep(has_p, tcy * LW0(-1, 0) * (V0(-1, 0) + Vp(-1, 0)));
-                rw += keep(pw, d1p * A(Pp, 5, 0, 0) * (Wp(0, 0) + 2.f * W0(0, 0)));
-                rw2 -= keep(has_p, d2 * LW0(0, 0) * Wp(0, 0));
-                rw += keep(has_m, d1 * LW0(0, 0) * Wm(0, 0));
-                rw2 -= keep(mw, d2m * A(Pm, 5, 0, 0) * (Wm(0, 0) + 2.f * W0(0, 0)));
-                ru += ru2;
-                rv += rv2;
-                rw += rw2;
-
-                if (J <= g.ny && I <= g.nx) {
-                    const long long o = g.origin + (long long)K * g.pk + (long long)J * g.pj + I;
-                    float bu = 0.f, bv = 0.f, bw = 0.f;
-                    if (accumulate) {
-                        bu = gu[o];
-                        bv = gv[o];
-                        bw = gw[o];
-                    } else if (add_lambda) {
-                        bu = A(P0, 3, 0, 0);
-                        bv = A(P0, 4, 0, 0);
-                        bw = A(P0, 5, 0, 0);
+                auto keep = [](bool c, float t) { return EDGE ? (c ? t : 0.f) : t; };
+                if (EDGE) {   // sensitivities of level K outside the scheme's outputs are ignored
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) {
+                        LU0m[x] = keep(lu0, LU0m[x]);
+                        LU0z[x] = keep(lu0, LU0z[x]);
+                        LU0p[x] = keep(lu0, LU0p[x]);
+                        LV0m[x] = keep(lu0, LV0m[x]);
+                        LV0z[x] = keep(lu0, LV0z[x]);
+                        LV0p[x] = keep(lu0, LV0p[x]);
+                        LW0m[x] = keep(lw0, LW0m[x]);
+                        LW0z[x] = keep(lw0, LW0z[x]);
+                        LW0p[x] = keep(lw0, LW0p[x]);
                     }
-                    gu[o] = fmaf(alpha, ru, bu);
-                    gv[o] = fmaf(alpha, rv, bv);
-                    gw[o] = fmaf(alpha, rw, bw);
                 }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int o = c + 1;   // the cell in the X arrays; o-1 and o+1 its x neighbours
+                    float a = 0.f, b = 0.f;
+                    // ---- gu
+                    a += tcx * LU0z[o + 1] * (U0z[o + 1] + 2.f * U0z[o]);
+                    b += tcx * LU0z[o] * U0z[o - 1];
+                    a -= tcx * LU0z[o - 1] * (U0z[o - 1] + 2.f * U0z[o]);
+                    b -= tcx * LU0z[o] * U0z[o + 1];
+                    a += tcy * LU0p[o] * (V0z[o] + V0z[o + 1]);
+                    b -= tcy * LU0m[o] * (V0m[o] + V0m[o + 1]);
+                    a += keep(pu, c1p * LUpz[o] * (W0z[o] + W0z[o + 1]));
+                    b -= keep(mu, c2m * LUmz[o] * (Wmz[o] + Wmz[o + 1]));
+                    a += tcx * LV0z[o + 1] * V0z[o];
+                    b += tcx * LV0m[o + 1] * V0m[o];
+                    a -= tcx * LV0z[o] * V0z[o + 1];
+                    b -= tcx * LV0m[o] * V0m[o + 1];
+                    a += tcx * LW0z[o + 1] * W0z[o];
+                    b -= tcx * LW0z[o] * W0z[o + 1];
+                    a += keep(mw, tcx * LWmz[o + 1] * Wmz[o]);
+                    b -= keep(mw, tcx * LWmz[o] * Wmz[o + 1]);
+                    ru[c] = a + b;
+                    // ---- gv
+                    a = 0.f;
+                    b = 0.f;
+                    a += tcy * LU0p[o] * U0z[o];
+                    b += tcy * LU0p[o - 1] * U0z[o - 1];
+                    a -= tcy * LU0z[o] * U0p[o];
+                    b -= tcy * LU0z[o - 1] * U0p[o - 1];
+                    a += tcx * LV0z[o + 1] * (U0z[o] + U0p[o]);
+                    b -= tcx * LV0z[o - 1] * (U0z[o - 1] + U0p[o - 1]);
+                    a += tcy * LV0p[o] * (V0p[o] + 2.f * V0z[o]);
+                    b += tcy * LV0z[o] * V0m[o];
+                    a -= tcy * LV0m[o] * (V0m[o] + 2.f * V0z[o]);
+                    b -= tcy * LV0z[o] * V0p[o];
+                    a += keep(pu, c1p * LVpz[o] * (W0z[o] + W0p[o]));
+                    b -= keep(mu, c2m * LVmz[o] * (Wmz[o] + Wmp[o]));
+                    a += tcy * LW0p[o] * W0z[o];
+                    b -= tcy * LW0z[o] * W0p[o];
+                    a += keep(mw, tcy * LWmp[o] * Wmz[o]);
+                    b -= keep(mw, tcy * LWmz[o] * Wmp[o]);
+                    rv[c] = a + b;
+                    // ---- gw
+                    a = 0.f;
+                    b = 0.f;
+                    a += keep(pu, c1p * LUpz[o] * U0z[o]);
+                    b += keep(pu, c1p * LUpz[o - 1] * U0z[o - 1]);
+                    a += keep(pu, c1p * LVpz[o] * V0z[o]);
+                    b += keep(pu, c1p * LVpm[o] * V0m[o]);
+                    a -= keep(has_p, c2 * LU0z[o] * Upz[o]);
+                    b -= keep(has_p, c2 * LU0z[o - 1] * Upz[o - 1]);
+                    a -= keep(has_p, c2 * LV0z[o] * Vpz[o]);
+                    b -= keep(has_p, c2 * LV0m[o] * Vpm[o]);
+                    a += keep(has_p, tcx * LW0z[o + 1] * (U0z[o] + Upz[o]));
+                    b -= keep(has_p, tcx * LW0z[o - 1] * (U0z[o - 1] + Upz[o - 1]));
+                    a += keep(has_p, tcy * LW0p[o] * (V0z[o] + Vpz[o]));
+                    b -= keep(has_p, tcy * LW0m[o] * (V0m[o] + Vpm[o]));
+                    a += keep(pw, d1p * LWpz[o] * (Wpz[o] + 2.f * W0z[o]));
+                    b -= keep(has_p, d2 * LW0z[o] * Wpz[o]);
+                    a += keep(has_m, d1 * LW0z[o] * Wmz[o]);
+                    b -= keep(mw, d2m * LWmz[o] * (Wmz[o] + 2.f * W0z[o]));
+                    rw[c] = a + b;
+                }
+            };
+            if (K >= 3 && K <= nz - 2)
+                body(std::false_type{});
+            else
+                body(std::true_type{});
+
+            if (valid) {
+                const long long o = g.origin + (long long)K * g.pk + (long long)J * g.pj + I0;
+                float4 bu = make_float4(0.f, 0.f, 0.f, 0.f), bv = bu, bw = bu;
+                if (accumulate) {
+                    bu = *reinterpret_cast<const float4*>(gu + o);
+                    bv = *reinterpret_cast<const float4*>(gv + o);
+                    bw = *reinterpret_cast<const float4*>(gw + o);
+                } else if (add_lambda) {   // the raw sensitivities of level K
+                    const float* q = P0 + (r)*kAdjBW + c0;
+                    bu = *reinterpret_cast<const float4*>(q + 3 * L::FIELD);
+                    bv = *reinterpret_cast<const float4*>(q + 4 * L::FIELD);
+                    bw = *reinterpret_cast<const float4*>(q + 5 * L::FIELD);
+                }
+                *reinterpret_cast<float4*>(gu + o) = make_float4(fmaf(alpha, ru[0], bu.x), fmaf(alpha, ru[1], bu.y),
+                                                                 fmaf(alpha, ru[2], bu.z), fmaf(alpha, ru[3], bu.w));
+                *reinterpret_cast<float4*>(gv + o) = make_float4(fmaf(alpha, rv[0], bv.x), fmaf(alpha, rv[1], bv.y),
+                                                                 fmaf(alpha, rv[2], bv.z), fmaf(alpha, rv[3], bv.w));
+                *reinterpret_cast<float4*>(gw + o) = make_float4(fmaf(alpha, rw[0], bw.x), fmaf(alpha, rw[1], bw.y),
+                                                                 fmaf(alpha, rw[2], bw.z), fmaf(alpha, rw[3], bw.w));
             }
         }
         __syncthreads();
@@ -382,13 +464,13 @@ __global__ void __launch_bounds__(32 * TY)
     }
 }
 
-constexpr int kAdjTY = 4, kAdjS = 5;
+constexpr int kAdjTY = 4, kAdjS = 5;   // rows per CTA, ring slots
 
 cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
                                float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
                                cudaStream_t s) {
     using L = AdjLayout<kAdjTY, kAdjS>;
-    auto kern = adjoint_tma_kernel<kAdjTY, kAdjS>;
+    auto kern = adjoint_vec_kernel<kAdjTY, kAdjS>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     AdjMaps m;
