@@ -185,17 +185,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, budget_s=10.0):
+def cpu_baseline(w, budget_s=10.0, slab=None):
     """The CPU oracle (FP64 plain C loop nest, one thread) on slabs of the
-    same workload: nx x 128 x nz grids from the same generator, repeated
-    until about budget_s seconds of CPU work."""
+    same workload: nx x 128 x nz grids, repeated until about budget_s seconds
+    of CPU work.  With `slab` (rows 1..128 of the benchmark's own inputs, with
+    their halo rows, and the GPU's FP32 and BF16-storage source terms on those
+    rows) the slab is the sample, and its first oracle result is also the
+    reference the GPU outputs are checked against: max|err| / max|ref| per
+    field, the largest of the three reported."""
     import oracle
     from paper_2301_13016_gb300 import inputs
     nx, nz = w["nx"], w["nz"]
     ny = 128
     c = inputs.make_coeffs(nz)
-    f = [x.numpy().astype(np.float64) for x in inputs.random_fields(nx, ny, nz)]
-    oracle.tendencies(*f, c)                      # load + warm
+    parity = None
+    if slab is None:
+        f = [x.numpy().astype(np.float64) for x in inputs.random_fields(nx, ny, nz)]
+        oracle.tendencies(*f, c)                      # load + warm
+    else:
+        f = slab["inputs"]
+        ref = oracle.tendencies(*f, c)
+        parity = {"sample": f"rows 1..{ny} of the workload (all {nx} columns, {nz} levels), FP64 oracle"}
+        for key, got in slab["outputs"].items():
+            parity[key] = max(float(np.abs(g - r[1:-1, 1:-1, 1:-1]).max() / np.abs(r[1:-1, 1:-1, 1:-1]).max())
+                              for g, r in zip(got, ref))
     cells, t_used, reps = 0, 0.0, 0
     while t_used < budget_s and reps < 200:
         t = time.perf_counter()
@@ -203,9 +216,12 @@ def cpu_baseline(w, budget_s=10.0):
         t_used += time.perf_counter() - t
         cells += nx * ny * nz
         reps += 1
-    return {"value": cells / t_used / 1e9, "unit": "Gcell/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle on {reps} x ({nx}x{ny}x{nz}) slabs of the same workload, "
-                      f"{t_used:.1f} s CPU, single thread"}
+    out = {"value": cells / t_used / 1e9, "unit": "Gcell/s", "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle on {reps} x ({nx}x{ny}x{nz}) slabs of the same workload, "
+                     f"{t_used:.1f} s CPU, single thread"}
+    if parity is not None:
+        out["parity"] = parity
+    return out
 
 
 def run_reference(args, rank, world):
@@ -283,6 +299,32 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peak()
     achieved = algo_bytes / launch_s / 1e9
 
+    # BF16 storage of the same inputs (FP32 arithmetic), and the check slab
+    bf16 = slab = None
+    if rank == 0:
+        rows = 128
+        slab = {"inputs": [grid.view(t)[:, 0:rows + 2, :].double().cpu().numpy() for t in dev],
+                "outputs": {"fp32_max_rel_err": [grid.view(o)[1:-1, 1:rows + 1, 1:-1].double().cpu().numpy()
+                                                 for o in outs]}}
+        g16 = pwlib.Grid(nx, ny, nz, dtype="bf16")
+        h16 = pwlib.PW(g16, c)
+        d16 = [g16.from_dense(grid.view(t)) for t in dev]
+        o16 = [g16.alloc() for _ in range(3)]
+        f16 = lambda: h16.tendencies(*d16, *o16, stream=stream)
+        for _ in range(3):
+            f16()
+        ms16 = _events_ms(f16, args.steps, stream)
+        h16.sync(stream)
+        slab["outputs"]["bf16_max_rel_err"] = [g16.view(o)[1:-1, 1:rows + 1, 1:-1].double().cpu().numpy()
+                                               for o in o16]
+        v16 = cells / (ms16 / 1e3) / 1e9
+        bf16 = {"value": v16, "unit": "Gcell/s", "ms_per_step": ms16, "vs_fp32": v16 / (value / world),
+                "launch_shape": h16.tma_config(), "bytes_per_cell": 12,
+                "roofline_frac": 12 * cells / (ms16 / 1e3) / 1e9 / peak,
+                "stated_error_bound": 1e-2, "error": "cpu_baseline.parity.bf16_max_rel_err"}
+        del h16, d16, o16
+        torch.cuda.empty_cache()
+
     # end to end through the host-buffer entry point: H2D + kernel + D2H per step
     hin = [t.cpu().pin_memory() for t in dev]
     hout = [torch.zeros(grid.alloc_elems, dtype=torch.float32).pin_memory() for _ in range(3)]
@@ -319,9 +361,12 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "bf16_storage": bf16,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(w, slab=slab)
+        if "parity" in line["cpu_baseline"]:
+            line["cpu_baseline"]["parity"]["fp32_bound"] = 1e-5
     print(json.dumps(line), flush=True)
 
 
