@@ -685,8 +685,10 @@ def form_latency64(args):
     outs = [g.alloc() for _ in range(3)]
     s = torch.cuda.Stream()
     res = {}
-    for lx, ty in ((32, 4), (16, 4)):
-        h.set_tma_config(ty, 4, 0, lanes_x=lx)
+    for lx, ty, nseg in ((0, 0, 0), (32, 4, 8), (16, 4, 8), (32, 4, 16), (16, 4, 16), (32, 8, 16), (32, 4, 32),
+                         (16, 4, 32)):
+        h.set_tma_config(ty, 4 if ty else 0, nseg, lanes_x=lx)   # (0, 0, 0): the automatic shape
+        lx, ty = h.tma_config()["lanes_x"], h.tma_config()["ty"]
         with torch.cuda.stream(s):
             for _ in range(3):
                 h.tendencies(*dev, *outs, stream=s)
@@ -700,7 +702,8 @@ def form_latency64(args):
         torch.cuda.synchronize()
         ms = _events_ms(graph.replay, 20, torch.cuda.current_stream()) / n_in
         direct = _events_ms(lambda: h.tendencies(*dev, *outs), 200, torch.cuda.current_stream())
-        res[f"lanes{lx}_ty{ty}"] = {"graph_us_per_call": ms * 1e3, "stream_us_per_call": direct * 1e3}
+        res[f"lanes{lx}_ty{ty}_nseg{h.tma_config()['nseg']}"] = {"graph_us_per_call": ms * 1e3,
+                                                               "stream_us_per_call": direct * 1e3}
     best = min(v["graph_us_per_call"] for v in res.values())
     _form_line(args, "latency64", "PW tendencies latency per call, 64^3 FP32 (graph replay)", best, "us",
                {"workload": "64x64x64 FP32 random 10*N(0,1); L2-resident, launch-bound (not a roofline point)"},
