@@ -464,7 +464,17 @@ __global__ void __launch_bounds__(32 * TY, 2)
     }
 }
 
-constexpr int kAdjTY = 4, kAdjS = 5;   // rows per CTA, ring slots
+// Rows per CTA and ring slots (levels k-1, k, k+1 resident, the rest in
+// flight).  Measured on GB300 (512^2 x 64): 4 rows / 5 slots 78.7, 4 / 4 79.5,
+// 5 / 4 83.1, 6 / 4 81.8 Gcell/s; 5 rows and 4 slots fit two CTAs of 160
+// threads (91 KB of shared memory, 165 registers) on an SM: 10 warps.
+#ifndef PW_ADJ_TY
+#define PW_ADJ_TY 5
+#endif
+#ifndef PW_ADJ_S
+#define PW_ADJ_S 4
+#endif
+constexpr int kAdjTY = PW_ADJ_TY, kAdjS = PW_ADJ_S;
 
 cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
                                float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
