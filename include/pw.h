@@ -124,13 +124,15 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
  * ty = rows per CTA, stages = planes buffered per CTA, nseg = CTAs along z
  * (0 = chosen from the grid and SM count), rows_per_thread = 1, or 2 (a
  * thread computes each cell together with the cell one row further on, in
- * packed FP32x2 arithmetic; same results bit for bit).  Any argument 0 keeps
- * the automatic choice, (lanes_x, ty, stages, cells, rows_per_thread) =
- * (32, 4, 4, 4, 1) for FP32 and (16, 8, 4, 8, 1) for 16-bit storage when nx
- * is a multiple of 8 (else (32, 4, 4, 4, 1)), and (16, 4, 4, 4, 1) when
- * nx <= 64; nseg as many as keep about two waves of CTAs, at least 2
- * levels each.  Instantiated (lanes_x, ty,
- * stages, cells, rows_per_thread): (32,4,4,4,1) (32,8,3,4,1) (32,8,4,4,1)
+ * packed FP32x2 arithmetic; same results bit for bit).  A shape given here is
+ * used for every call, its zero fields at (lanes_x, ty, stages, cells,
+ * rows_per_thread) = (32, 4, 4, 4, 1); all zero restores the automatic
+ * choice, which depends on the call: (32, 4, 4, 4, 1) for FP32;
+ * (32, 8, 4, 4, 2) for the source terms with 16-bit storage; (16, 8, 4, 8, 1)
+ * for fused steps with 16-bit storage when nx is a multiple of 8 (else
+ * (32, 4, 4, 4, 1)); (16, 4, 4, 4, 1) when nx <= 64; nseg as many as keep
+ * about two waves of CTAs, at least 2 levels each.  Instantiated (lanes_x,
+ * ty, stages, cells, rows_per_thread): (32,4,4,4,1) (32,8,3,4,1) (32,8,4,4,1)
  * (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1) (16,8,4,4,1), and for 16-bit
  * storage also (16,4,4,8,1) (16,8,4,8,1) (32,8,4,4,2) (32,16,4,4,2)
  * (16,8,4,4,2); others, and cells = 8 with nx not a multiple of 8, give
@@ -141,10 +143,11 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
 
 /*
  * The launch shape the TMA k-march kernel will use on this handle (the
- * automatic choice, or what pw_set_tma_config fixed): out = {lanes_x, cells,
- * ty, stages, nseg, rows_per_thread}.
+ * automatic choice, or what pw_set_tma_config fixed) for pw_tendencies
+ * (step = 0) or pw_step (step != 0): out = {lanes_x, cells, ty, stages, nseg,
+ * rows_per_thread}.
  */
-pw_status_t pw_get_tma_config(pw_handle_t h, int32_t out[6]);
+pw_status_t pw_get_tma_config(pw_handle_t h, int32_t step, int32_t out[6]);
 
 /*
  * Temporal blocking of pw_step.  steps_per_pass: 1 = one step per kernel

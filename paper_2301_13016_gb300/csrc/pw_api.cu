@@ -78,7 +78,7 @@ struct pw_handle_s {
     // user overrides: every field 0 = automatic (nc and rp too, whose struct
     // defaults are the values a launch uses)
     TmaConfig tma_user{0, 0, 0, 0, 0, 0, 0, 0};
-    TmaConfig tma_auto{0, 0, 0, 0};   // cached automatic choice (ty == 0: not chosen yet)
+    TmaConfig tma_auto[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};   // per mode (source terms, steps); ty == 0: not chosen yet
     int steps_per_pass = 0;           // pw_step temporal blocking: 0 auto (= 1), 1, 2
     Step2Config step2_user{0, 0, 0, 0};
     Step2Config step2_auto{0, 0, 0, 0};   // ty == 0: not chosen yet
@@ -206,40 +206,67 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
     return PW_OK;
 }
 
-// Launch shape of the TMA kernel: user overrides, else 32 lanes x 4 cells x
-// 4 rows for FP32 and 16 lanes x 8 cells x 8 rows for 16-bit storage (nx a
-// multiple of 8), 16 lanes x 4 cells x 4 rows when nx <= 64, 4 stages (the
-// fastest measured shapes on GB300), and enough k segments for about two
-// waves of CTAs over the SMs.
-static TmaConfig choose_tma(pw_handle_t h) {
-    if (h->tma_auto.ty) return h->tma_auto;
+// Launch shape of the TMA kernel for the source terms (step = false) or the
+// fused step (step = true).  A shape the user fixed (pw_set_tma_config) is used
+// as given, unset fields at the scalar defaults (32 lanes x 4 cells x 4 rows, 4
+// stages, one row per thread).  Otherwise the shape measured fastest on GB300
+// (2048^2 x 64):
+//   FP32:                       32 lanes x 4 cells x 4 rows (HBM-bound);
+//   16-bit, source terms:       32 lanes x 4 cells x 8 rows, two rows per
+//                               thread in packed FP32x2 (BF16 325, FP16 299
+//                               Gcell/s; one row per thread: 305, 296);
+//   16-bit, steps (nx % 8 = 0): 16 lanes x 8 cells x 8 rows (BF16 279, FP16
+//                               267 Gcell-steps/s; two rows: 266, 247);
+//   nx <= 64:                   16 lanes x 4 cells x 4 rows;
+// 4 stages, and k segments doubled while the CTAs cover fewer than about two
+// waves over the SMs, down to 2 levels per segment.
+static TmaConfig choose_tma(pw_handle_t h, bool step) {
+    TmaConfig& cache = h->tma_auto[step ? 1 : 0];
+    if (cache.ty) return cache;
+    const TmaConfig& u = h->tma_user;
+    const pw_grid_t& gr = h->grid;
     TmaConfig c;
-    // 16-bit storage with nx a multiple of 8: 8 cells per thread, 16 lanes per
-    // row; grids at most 64 columns wide: 64-column tiles
-    const bool small = h->grid.nx <= 64;
-    const bool wide = dtype_size(h->grid.dtype) == 2 && h->grid.nx % 8 == 0 && !small;
-    c.lx = h->tma_user.lx ? h->tma_user.lx : ((wide || small) ? 16 : 32);
-    c.nc = h->tma_user.nc ? h->tma_user.nc : (wide ? 8 : 4);
-    c.ty = h->tma_user.ty ? h->tma_user.ty : (wide ? 8 : 4);
-    c.rp = h->tma_user.rp ? h->tma_user.rp : 1;
-    c.stages = h->tma_user.stages ? h->tma_user.stages : 4;
-    if (h->tma_user.nseg) {
-        c.nseg = h->tma_user.nseg;
+    if (u.lx || u.nc || u.ty || u.stages || u.rp) {
+        c.lx = u.lx ? u.lx : 32;
+        c.nc = u.nc ? u.nc : 4;
+        c.ty = u.ty ? u.ty : 4;
+        c.stages = u.stages ? u.stages : 4;
+        c.rp = u.rp ? u.rp : 1;
+    } else {
+        const bool half = dtype_size(gr.dtype) == 2;
+        c.lx = 32;
+        c.nc = 4;
+        c.ty = 4;
+        c.stages = 4;
+        c.rp = 1;
+        if (gr.nx <= 64) {
+            c.lx = 16;
+        } else if (half && !step) {
+            c.ty = 8;
+            c.rp = 2;
+        } else if (half && step && gr.nx % 8 == 0) {
+            c.lx = 16;
+            c.nc = 8;
+            c.ty = 8;
+        }
+    }
+    if (u.nseg) {
+        c.nseg = u.nseg;
     } else {
         const long long tiles =
-            (long long)((h->grid.nx + c.nc * c.lx - 1) / (c.nc * c.lx)) * ((h->grid.ny + c.ty - 1) / c.ty);
-        int bps = tma_blocks_per_sm(h->grid.dtype, c);
+            (long long)((gr.nx + c.nc * c.lx - 1) / (c.nc * c.lx)) * ((gr.ny + c.ty - 1) / c.ty);
+        int bps = tma_blocks_per_sm(gr.dtype, c);
         if (bps < 1) bps = 1;
         const long long slots = (long long)h->num_sms * bps;
         // down to 2 levels per segment: a small grid is a short serial march
         // (64^3 FP32 in a CUDA graph: 7.0 us per call with 8 segments, 4.0
         // with 32 on 64-column tiles); large grids stop at one segment
         int nseg = 1;
-        while (tiles * nseg < 2 * slots && h->grid.nz / (nseg * 2) >= 2) nseg *= 2;
+        while (tiles * nseg < 2 * slots && gr.nz / (nseg * 2) >= 2) nseg *= 2;
         c.nseg = nseg;
     }
-    if (c.nseg > h->grid.nz / 2) c.nseg = std::max(1, h->grid.nz / 2);
-    h->tma_auto = c;
+    if (c.nseg > gr.nz / 2) c.nseg = std::max(1, gr.nz / 2);
+    cache = c;
     return c;
 }
 
@@ -390,7 +417,7 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
     h->tma_user = TmaConfig{lanes_x, ty, stages, nseg};
     h->tma_user.nc = cells;
     h->tma_user.rp = rows_per_thread;
-    h->tma_auto = TmaConfig{0, 0, 0, 0};
+    h->tma_auto[0] = h->tma_auto[1] = TmaConfig{0, 0, 0, 0};
     for (auto& m : h->maps) m.ptr = nullptr;
     return PW_OK;
 }
@@ -434,9 +461,9 @@ static Step2Config choose_step2(pw_handle_t h) {
     return c;
 }
 
-pw_status_t pw_get_tma_config(pw_handle_t h, int32_t out[6]) {
+pw_status_t pw_get_tma_config(pw_handle_t h, int32_t step, int32_t out[6]) {
     if (!h || !out) return fail(PW_ERR_ARG, "handle or out is NULL");
-    const TmaConfig c = choose_tma(h);
+    const TmaConfig c = choose_tma(h, step != 0);
     out[0] = c.lx;
     out[1] = c.nc;
     out[2] = c.ty;
@@ -480,7 +507,7 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
     }
     if (use_tma) {
-        TmaConfig c = choose_tma(h);
+        TmaConfig c = choose_tma(h, false);
         CUtensorMap maps[3];
         for (int q = 0; q < 3; ++q) {
             pw_status_t st = encode_map(h, ins[q], ox, c.lx, c.ty, &maps[q], c.nc);
@@ -564,7 +591,7 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         for (int q = 0; q < 6; ++q)
             if (!(scale[q] > 0.f) || !(scale[q] < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
     make_scales(scale, &sc, &scaled);
-    TmaConfig cfg = choose_tma(h);
+    TmaConfig cfg = choose_tma(h, false);
     cfg.nseg = C;
     cfg.seg_count = 1;
     CUtensorMap maps[3];
@@ -661,7 +688,7 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     // by instruction issue, not HBM, and runs slower per step
     const bool use_tb2 = tb2_ok && h->steps_per_pass == 2;
     TmaConfig c{};
-    if (use_tma) c = choose_tma(h);
+    if (use_tma) c = choose_tma(h, true);
     Step2Config c2{};
     if (use_tb2 && nsteps >= 2) c2 = choose_step2(h);
     int done = 0, passes = 0, kind = use_tma ? 2 : 1;

@@ -271,18 +271,20 @@ struct VOps<float2> {
 // by every k-march kernel: single step, two-step temporal blocking, batch).
 //
 // MarchRegs is what a thread carries from level kk to kk+1: the level-kk rows
-// it loaded as level kk+1 on the previous step, the level kk-1 values at its
-// cells (a rolling window in z) and the three vertical pair sums of the upper
-// fluxes, which are the lower pair sums of the next level.
+// it loaded as level kk+1 on the previous step, and the lower vertical flux
+// products of level kk, u(kk-1)*(w(kk-1,i) + w(kk-1,i+1)) and its v and w
+// counterparts.  Both factors of each product are known one level earlier
+// (the level's own values and its upper pair sums), so the product is formed
+// there and carried instead of the two factors: the same operation on the
+// same operands, three carried arrays instead of six.
 template <int NC, typename V = float>
 struct MarchRegs {
     V u0[NC], v0[NC], vs[NC], w0[NC];   // level kk: u, v, w in row r; vs = v in row r-1
-    V ud[NC], vd[NC], wd[NC];           // level kk-1 at the cells
-    V pzu[NC], pzv[NC], pzw[NC];        // lower vertical pair sums of level kk
+    V pdu[NC], pdv[NC], pdw[NC];        // lower vertical flux products of level kk
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            ud[c] = vd[c] = wd[c] = pzu[c] = pzv[c] = pzw[c] = VOps<V>::zero();
+            pdu[c] = pdv[c] = pdw[c] = VOps<V>::zero();
             u0[c] = v0[c] = vs[c] = w0[c] = VOps<V>::zero();
         }
     }
@@ -401,13 +403,13 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
             // su
             V x = O::mul(tcx, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
             x = O::fma(tcy, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
-            ru[c] = O::fma(tz1, O::mul(st.ud[c], st.pzu[c]), x);
+            ru[c] = O::fma(tz1, st.pdu[c], x);
             // sv
             V y = O::mul(tcx, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
             y = O::fma(tcy,
                        O::fma(O::neg(vn[c]), O::add(Vv[c + 1], vn[c]), O::mul(st.vs[c], O::add(Vv[c + 1], st.vs[c]))),
                        y);
-            rv[c] = O::fma(tz1, O::mul(st.vd[c], st.pzv[c]), y);
+            rv[c] = O::fma(tz1, st.pdv[c], y);
         }
         if (have_up) {   // kk < nz: upper vertical fluxes and sw
             const V ntz2 = O::splat(-__ldg(tz + nzp2 + kk));
@@ -420,7 +422,7 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
                 V z = O::mul(tcx, O::fma(O::neg(W[c + 2]), rx[c + 1], O::mul(W[c], rx[c])));
                 z = O::fma(tcy, O::fma(O::neg(wn[c]), O::add(Vv[c + 1], vu[c]), O::mul(ws[c], O::add(st.vs[c], vus[c]))),
                            z);
-                z = O::fma(td1, O::mul(st.wd[c], st.pzw[c]), z);
+                z = O::fma(td1, st.pdw[c], z);
                 rw[c] = O::fma(ntd2, O::mul(wu[c], pzw_n[c]), z);
             }
         }
@@ -428,15 +430,12 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 
     out(ru, rv, rw, st.u0, st.v0, st.w0);
 
-    // roll: level kk becomes level k-1, level kk+1 becomes level kk
+    // roll: the lower flux products of level kk+1, then level kk+1 becomes level kk
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        st.ud[c] = st.u0[c];
-        st.vd[c] = st.v0[c];
-        st.wd[c] = st.w0[c];
-        st.pzu[c] = pzu_n[c];
-        st.pzv[c] = pzv_n[c];
-        st.pzw[c] = pzw_n[c];
+        st.pdu[c] = O::mul(st.u0[c], pzu_n[c]);   // u(k) * (w(k,i) + w(k,i+1))
+        st.pdv[c] = O::mul(st.v0[c], pzv_n[c]);   // v(k) * (w(k,j) + w(k,j+1))
+        st.pdw[c] = O::mul(st.w0[c], pzw_n[c]);   // w(k) * (w(k) + w(k+1))
         st.u0[c] = uu[c];
         st.v0[c] = vu[c];
         st.vs[c] = vus[c];

@@ -54,7 +54,7 @@ SIGNATURES = [
     ("pw_set_kernel", ctypes.c_int, [_VP, _I32]),
     ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
     ("pw_set_step_blocking", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
-    ("pw_get_tma_config", ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
+    ("pw_get_tma_config", ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I32)]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
@@ -240,10 +240,11 @@ class PW:
         _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg),
                                        int(rows)), "pw_set_tma_config")
 
-    def tma_config(self):
-        """The k-march launch shape in use: dict(lanes_x, cells, ty, stages, nseg, rows)."""
+    def tma_config(self, step=False):
+        """The k-march launch shape tendencies() (or step(), with step=True)
+        uses: dict(lanes_x, cells, ty, stages, nseg, rows)."""
         out = (_I32 * 6)()
-        _check(lib().pw_get_tma_config(self.h, out), "pw_get_tma_config")
+        _check(lib().pw_get_tma_config(self.h, 1 if step else 0, out), "pw_get_tma_config")
         return dict(zip(("lanes_x", "cells", "ty", "stages", "nseg", "rows"), list(out)))
 
     def set_step_blocking(self, steps_per_pass=0, ty=0, stages=0, ctas_per_sm=0, nseg=0):

@@ -169,19 +169,34 @@ def test_two_rows_per_thread_needs_16bit_storage():
 
 
 def test_automatic_launch_shapes():
-    """The automatic k-march shape: 32 lanes x 4 cells x 4 rows for FP32 (and
-    for 16-bit storage when nx is not a multiple of 8), 16 lanes x 8 cells x
-    8 rows for 16-bit storage, 16 lanes x 4 cells x 4 rows for grids at most
-    64 columns wide; pw_get_tma_config reports what a launch uses."""
+    """The automatic k-march shape per call: FP32 32 lanes x 4 cells x 4 rows;
+    16-bit source terms 32 x 4 x 8 with two rows per thread; 16-bit steps
+    16 x 8 x 8 (nx a multiple of 8, else the FP32 shape); 16 x 4 x 4 for
+    grids at most 64 columns wide, with k segments of 2 levels; a shape set
+    by pw_set_tma_config is used as given (zero fields at the scalar
+    defaults) for every call."""
     c = inputs.make_coeffs(8)
-    pick = lambda g: {k: v for k, v in pwlib.PW(g, c).tma_config().items() if k != "nseg"}
-    assert pick(pwlib.Grid(256, 64, 8)) == dict(lanes_x=32, cells=4, ty=4, stages=4, rows=1)
+
+    def pick(g, step=False):
+        return {k: v for k, v in pwlib.PW(g, c).tma_config(step).items() if k != "nseg"}
+
+    f32 = dict(lanes_x=32, cells=4, ty=4, stages=4, rows=1)
+    for step in (False, True):
+        assert pick(pwlib.Grid(256, 64, 8), step) == f32
     for dtype in ("bf16", "f16"):
-        assert pick(pwlib.Grid(256, 64, 8, dtype=dtype)) == dict(lanes_x=16, cells=8, ty=8, stages=4, rows=1)
-        assert pick(pwlib.Grid(260, 64, 8, dtype=dtype)) == dict(lanes_x=32, cells=4, ty=4, stages=4, rows=1)
-    for dtype in ("f32", "bf16"):   # small grids: 64-column tiles, k segments of 2 levels
-        assert pwlib.PW(pwlib.Grid(64, 64, 8, dtype=dtype), c).tma_config() == dict(
-            lanes_x=16, cells=4, ty=4, stages=4, nseg=4, rows=1)
+        for nx in (256, 260):
+            assert pick(pwlib.Grid(nx, 64, 8, dtype=dtype)) == dict(lanes_x=32, cells=4, ty=8, stages=4, rows=2)
+        assert pick(pwlib.Grid(256, 64, 8, dtype=dtype), True) == dict(lanes_x=16, cells=8, ty=8, stages=4, rows=1)
+        assert pick(pwlib.Grid(260, 64, 8, dtype=dtype), True) == f32
+    for dtype in ("f32", "bf16"):
+        for step in (False, True):
+            assert pwlib.PW(pwlib.Grid(64, 64, 8, dtype=dtype), c).tma_config(step) == dict(
+                lanes_x=16, cells=4, ty=4, stages=4, nseg=4, rows=1)
     h = pwlib.PW(pwlib.Grid(256, 64, 8, dtype="bf16"), c)
     h.set_tma_config(8, 4, 2, lanes_x=32, cells=4, rows=2)
-    assert h.tma_config() == dict(lanes_x=32, cells=4, ty=8, stages=4, nseg=2, rows=2)
+    for step in (False, True):
+        assert h.tma_config(step) == dict(lanes_x=32, cells=4, ty=8, stages=4, nseg=2, rows=2)
+    h.set_tma_config(ty=8)
+    assert h.tma_config() == dict(f32, ty=8, nseg=h.tma_config()["nseg"])
+    h.set_tma_config()
+    assert pick(pwlib.Grid(256, 64, 8, dtype="bf16")) == {k: v for k, v in h.tma_config().items() if k != "nseg"}
