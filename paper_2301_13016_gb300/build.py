@@ -18,7 +18,7 @@ SOURCES = ["pw_api.cu", "pw_tend.cu", "pw_step.cu", "pw_step2.cu", "pw_adjoint.c
 HEADERS = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
     [os.path.join(ROOT, "include", "pw.h")]
 NVCC = os.environ.get("NVCC", "nvcc")
-EXTRA = os.environ.get("PW_NVCC_EXTRA", "").split()     # e.g. kernel knobs -DPW_TMA_UNROLL=0
+EXTRA = os.environ.get("PW_NVCC_EXTRA", "").split()     # kernel knobs, e.g. -DPW_TMA_REGS8=168
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 

@@ -502,6 +502,10 @@ struct TmaLayout {
 #ifndef PW_TMA_MAX_MINB
 #define PW_TMA_MAX_MINB 2
 #endif
+// Register target of the 8-cells-a-thread shapes (8 x 1 or 4 x 2).
+#ifndef PW_TMA_REGS8
+#define PW_TMA_REGS8 168
+#endif
 // Levels per iteration of the k-march loop (1, 2 or 3).  On GB300 2 and 3
 // were 15-25 % slower for every shape and storage type (more registers,
 // fewer resident CTAs), so 1.
@@ -520,15 +524,16 @@ struct TmaLayout {
 
 // Resident CTAs per SM the register budget is sized for: what shared memory
 // and the thread limit allow, at most PW_TMA_MAX_MINB for 4 cells a thread;
-// 8 cells a thread (8 x 1 or 4 x 2) get 168 registers, which measured best
-// on GB300 (16 lanes x 8 cells x 4 rows: 269 -> 295 Gcell/s for BF16 against
-// the compiler's 210 registers, as more CTAs per SM hide more latency).
+// 8 cells a thread (8 x 1 or 4 x 2) get PW_TMA_REGS8 = 168 registers, which
+// measured best on GB300 (16 lanes x 8 cells x 4 rows: 269 -> 295 Gcell/s for
+// BF16 against the compiler's 210 registers, as more CTAs per SM hide more
+// latency; 128 spills and 200 leaves 2 CTAs per SM, both slower).
 template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1>
 constexpr int tma_min_blocks() {
     using L = TmaLayout<T, LX, TY, S, NC, RP>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
-    constexpr int by_regs = NC * RP == 8 ? 65536 / (L::THREADS * 168) : PW_TMA_MAX_MINB;
+    constexpr int by_regs = NC * RP == 8 ? 65536 / (L::THREADS * PW_TMA_REGS8) : PW_TMA_MAX_MINB;
     constexpr int m0 = by_smem < by_threads ? by_smem : by_threads;
     constexpr int m = m0 < by_regs ? m0 : by_regs;
     return m < 1 ? 1 : m;
