@@ -38,7 +38,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.m
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
                   for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
 FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16", "precision",
-         "batch", "adjoint", "latency64"]
+         "batch", "adjoint", "latency64", "hostlink"]
 
 
 def parse():
@@ -710,6 +710,62 @@ def form_latency64(args):
                {"dtype": "f32", "higher_is_better": False, "shapes": res, "gcells_at_best": g.cells / best / 1e3})
 
 
+def form_hostlink(args):
+    """The bound of the end-to-end number: the host link.  Times the copies
+    pw_tendencies_host makes (levels 1..nz of u, v, w in, su, sv, sw out, from
+    and to pinned host memory, 2048 x 2048 x 64 FP32) one direction at a time
+    and both at once, and the host path itself, which pipelines them with the
+    kernel; the ratio of the last two is how close the path is to its bound."""
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs
+    nx = ny = 2048
+    nz = 64
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, inputs.make_coeffs(nz))
+    n = g.alloc_elems
+    gen = torch.Generator().manual_seed(2301)
+    hin = [torch.randn(n, generator=gen, dtype=torch.float32).pin_memory() for _ in range(3)]
+    hout = [torch.zeros(n, dtype=torch.float32).pin_memory() for _ in range(3)]
+    din = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    dout = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    lo = g.origin + g.pitch_k + (1 - g.halo) * g.pitch_j + 1 - g.halo
+    hi = g.origin + nz * g.pitch_k + (g.ny + g.halo) * g.pitch_j + g.nx + g.halo + 1
+    gb = 3 * (hi - lo) * 4 / 1e9
+
+    def wall(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / reps
+
+    def h2d():
+        with torch.cuda.stream(s_in):
+            for q in range(3):
+                din[q][lo:hi].copy_(hin[q][lo:hi], non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            for q in range(3):
+                hout[q][lo:hi].copy_(dout[q][lo:hi], non_blocking=True)
+
+    reps = max(2, min(args.steps, 10))
+    t_in, t_out = wall(h2d, reps), wall(d2h, reps)
+    t_both = wall(lambda: (h2d(), d2h()), reps)
+    t_path = wall(lambda: h.tendencies_host(*hin, *hout), reps)
+    val = g.cells / t_path / 1e9
+    _form_line(args, "hostlink", "PW tendencies end to end through host buffers, against the host-link bound", val,
+               "Gcell/s", {"workload": f"{nx}x{ny}x{nz} FP32, pinned host buffers, {gb:.2f} GB each way per call"},
+               {"dtype": "f32", "ms_per_step": t_path * 1e3,
+                "copy_gbs": {"h2d_alone": gb / t_in, "d2h_alone": gb / t_out, "each_way_both_at_once": gb / t_both},
+                "copy_only_ms": t_both * 1e3, "bound_gcells": g.cells / t_both / 1e9,
+                "frac_of_link_bound": t_both / t_path, "h2d_bytes_per_step": int(gb * 1e9),
+                "d2h_bytes_per_step": int(gb * 1e9)})
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -724,7 +780,8 @@ def main():
              "step2": lambda: form_step(args, "f32", 2), "step2-bf16": lambda: form_step(args, "bf16", 2),
              "step2-f16": lambda: form_step(args, "f16", 2),
              "precision": lambda: form_precision(args), "batch": lambda: form_batch(args),
-             "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args)}[args.form]()
+             "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args),
+             "hostlink": lambda: form_hostlink(args)}[args.form]()
     finally:
         if world > 1:
             import torch.distributed as dist
