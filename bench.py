@@ -418,7 +418,7 @@ def form_tend_lowp(args, dtype):
     nx = ny = 2048
     nz = 64
     stream = torch.cuda.current_stream()
-    ref = _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
+    ref = None if args.skip_fp32_ref else _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
     c = inputs.make_coeffs(nz)
     g = pwlib.Grid(nx, ny, nz, dtype=dtype)
     h = pwlib.PW(g, c)
@@ -438,13 +438,13 @@ def form_tend_lowp(args, dtype):
     _form_line(args, f"tend-{dtype}", f"PW tendencies Gcell/s, {dtype.upper()} storage (FP32 arithmetic)", val,
                "Gcell/s", {"workload": f"{nx}x{ny}x{nz} random 10*N(0,1), {dtype} storage, per-field power-of-two scales",
                            "scales": list(sc)},
-               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref, "fp32_form_gcells": ref,
+               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": 12},
                 "gpu_launches": args.steps})
 
 
-STEP2_SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (16, 3, 1)]
+STEP2_SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (12, 3, 1), (16, 3, 1), (16, 4, 1)]
 
 
 def form_step(args, dtype, spp=1):
@@ -456,7 +456,7 @@ def form_step(args, dtype, spp=1):
     nx = ny = 2048
     nz = 64
     stream = torch.cuda.current_stream()
-    ref = _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
+    ref = None if args.skip_fp32_ref else _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
     c = inputs.make_coeffs(nz)
     g = pwlib.Grid(nx, ny, nz, dtype=dtype, halo=spp)
     h = pwlib.PW(g, c)
@@ -489,7 +489,8 @@ def form_step(args, dtype, spp=1):
     peak, kind = measured_peak()
     achieved = bpcs * g.cells / (ms / 1e3) / 1e9
     name = ("step" if spp == 1 else "step2") + ("" if dtype == "f32" else f"-{dtype}")
-    extra = {"dtype": dtype, "ms_per_step": ms, "vs_fp32_tend_form": val / ref, "fp32_tend_gcells": ref,
+    extra = {"dtype": dtype, "ms_per_step": ms, "vs_fp32_tend_form": val / ref if ref else None,
+             "fp32_tend_gcells": ref,
              "steps_per_pass": spp, "last_kernel": kernel,
              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                           "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell_step": bpcs},

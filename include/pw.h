@@ -161,8 +161,8 @@ pw_status_t pw_get_tma_config(pw_handle_t h, int32_t step, int32_t out[6]);
  * state per CTA (ty - 2 output rows), stages = input planes in flight,
  * ctas_per_sm = the register budget (1: up to 255 registers a thread; 2: 128,
  * part of the state in local memory), nseg = CTAs along z.  Instantiated
- * (ty, stages, ctas_per_sm): (8,3,1) (8,3,2) (8,4,1) (16,3,1); others give
- * PW_ERR_UNSUPPORTED.  Automatic shape: (8, 3, 1).
+ * (ty, stages, ctas_per_sm): (8,3,1) (8,3,2) (8,4,1) (12,3,1) (16,3,1) (16,4,1);
+ * others give PW_ERR_UNSUPPORTED.  Automatic shape: (16, 3, 1).
  */
 pw_status_t pw_set_step_blocking(pw_handle_t h, int32_t steps_per_pass, int32_t ty, int32_t stages,
                                  int32_t ctas_per_sm, int32_t nseg);

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
 }
 
 // Instantiated (rows per CTA, stages, register budget in resident CTAs).
-#define PW_TB2_CONFIGS(X) X(8, 3, 1) X(8, 3, 2) X(8, 4, 1) X(16, 3, 1)
+#define PW_TB2_CONFIGS(X) X(8, 3, 1) X(8, 3, 2) X(8, 4, 1) X(12, 3, 1) X(16, 3, 1) X(16, 4, 1)
 
 template <typename T, int TY, int S, int MINB, bool SC>
 static cudaError_t launch_tb2_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,

@@ -25,7 +25,7 @@ from gpu_util import NAN, interior
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (16, 3, 1)]
+SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (12, 3, 1), (16, 3, 1), (16, 4, 1)]
 
 
 def _fields(nx, ny, nz, smooth):
@@ -169,7 +169,7 @@ def test_two_step_requirements():
     g2 = pwlib.Grid(nx, ny, nz, halo=2)
     h2 = pwlib.PW(g2, c)
     with pytest.raises(pwlib.PwError) as e:
-        h2.set_step_blocking(2, ty=12)
+        h2.set_step_blocking(2, ty=10)
     assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
     with pytest.raises(pwlib.PwError) as e:
         h2.set_step_blocking(3)
