@@ -116,10 +116,15 @@ def measured_peak():
 
 
 def kernel_source_hash():
+    """sha256[:16] of the tendency kernel's sources with comments and
+    whitespace removed, so that only a change to the code voids a profile."""
     h = hashlib.sha256()
     for path in KERNEL_SOURCES:
-        with open(path, "rb") as fh:
-            h.update(fh.read())
+        with open(path) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -506,12 +506,6 @@ struct TmaLayout {
 #ifndef PW_TMA_REGS8
 #define PW_TMA_REGS8 168
 #endif
-// Levels per iteration of the k-march loop (1, 2 or 3).  On GB300 2 and 3
-// were 15-25 % slower for every shape and storage type (more registers,
-// fewer resident CTAs), so 1.
-#ifndef PW_MARCH_UNROLL
-#define PW_MARCH_UNROLL 1
-#endif
 // How a plane slot is handed back to the copy engine after a level:
 // 1 = each warp counts itself out on the slot (an acquire-release atomic) and
 //     the last one refills it, so warps may drift up to S-1 levels apart;
@@ -756,15 +750,14 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
 #endif
     };
 
-    // PW_MARCH_UNROLL levels per loop iteration: the carried rows then rotate
-    // through registers by renaming instead of register moves
+    // One level per loop iteration.  (Two or three per iteration, so that the
+    // carried rows rotate by register renaming instead of moves, cost
+    // registers and CTAs per SM and measured 15-25 % slower on GB300; reloading
+    // the level's rows from the staged plane instead of carrying them gained
+    // nothing either.)
     bool aborted = false;
-#pragma unroll 1
-    for (int kk = pb; kk <= ke && !aborted; kk += PW_MARCH_UNROLL) {
-#pragma unroll
-        for (int u = 0; u < PW_MARCH_UNROLL; ++u)
-            if (!aborted && kk + u <= ke && !level(kk + u)) aborted = true;
-    }
+    for (int kk = pb; kk <= ke && !aborted; ++kk)
+        if (!level(kk)) aborted = true;
 
 #if PW_MARCH_SPLIT_ARRIVE
     // every warp has left the march (each wait is bounded): the ring is free
