@@ -297,6 +297,16 @@ def run_ours(args, rank, world, local):
     h.sync(stream)
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, world)
+    # per-launch times (events between launches, outside the timed region above)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(min(args.steps, 50) + 1)]
+    evs[0].record(stream)
+    for e in evs[1:]:
+        h.tendencies(*dev, *outs, stream=stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in zip(evs[:-1], evs[1:])]
+    timing = {"launches": len(per), "mean_ms": statistics.mean(per), "median_ms": statistics.median(per),
+              "min_ms": min(per), "max_ms": max(per)}
     cells = grid.cells
     value = whole_job_rate(cells * args.steps, world, ms / 1e3) / 1e9   # Gcell/s, whole job
     launch_s = ms / 1e3 / args.steps                                  # one kernel per step
@@ -350,6 +360,7 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return
+    traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -361,8 +372,11 @@ def run_ours(args, rank, world, local):
         "hbm_frac_of_measured": achieved / peak,
         "gflops_useful": value * FLOPS_PER_CELL,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes},
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_bytes_per_cell": traffic / cells if traffic else None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                     "algorithmic_bytes_per_cell": BYTES_PER_CELL_F32},
+        "launch_timing": timing,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

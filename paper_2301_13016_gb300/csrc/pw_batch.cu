@@ -26,8 +26,25 @@ struct BatchGridDev {
     void* o[3];
 };
 
+// Resident CTAs per SM the batch kernel's register budget is sized for (at
+// most what shared memory and the thread limit allow; 0: as the single-grid
+// k-march).  On GB300 (512-grid batch) 8 or 10 for the 64-thread tiles, 116
+// or 95 registers instead of 150, ran at 221 against 224 Gcell/s.
+#ifndef PW_BATCH_MINB
+#define PW_BATCH_MINB 0
+#endif
+template <typename T, int LX, int TY, int S>
+constexpr int batch_min_blocks() {
+    using L = TmaLayout<T, LX, TY, S>;
+    constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
+    constexpr int by_threads = 2048 / L::THREADS;
+    constexpr int m = by_smem < by_threads ? by_smem : by_threads;
+    constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S>();
+    return want < m ? want : m;
+}
+
 template <typename T, int LX, int TY, int S, bool SCALED>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (tma_min_blocks<T, LX, TY, S>()))
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (batch_min_blocks<T, LX, TY, S>()))
     tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                      const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
                      int* __restrict__ err) {
