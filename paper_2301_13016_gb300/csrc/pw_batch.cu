@@ -43,7 +43,7 @@ constexpr int batch_min_blocks() {
     return want < m ? want : m;
 }
 
-template <typename T, int LX, int TY, int S, bool SCALED>
+template <typename T, int LX, int TY, int S>
 __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (batch_min_blocks<T, LX, TY, S>()))
     tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                      const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
@@ -70,21 +70,20 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (batch_min_b
         const int ke = (int)(((long long)(seg + 1) * nz) / bg.nseg);
         const CoefDev cf{bg.tcx, bg.tcy, bg.tz};
         const CUtensorMap* m = maps + 3 * (size_t)item.x;
-        if (!march_tile<T, LX, TY, S, SCALED, MODE_TEND>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1],
-                                                         (T*)bg.o[2], bg.g, bg.ox, sc, cf, 0.f, bx, by, kb, ke,
-                                                         ring, err))
+        if (!march_tile<T, LX, TY, S, MODE_TEND>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1], (T*)bg.o[2],
+                                                 bg.g, bg.ox, fold_coef(cf, sc), 0.f, bx, by, kb, ke, ring, err))
             break;
     }
 }
 
 #define PW_BATCH_CONFIGS(X) X(32, 4, 4) X(32, 8, 4) X(16, 4, 4) X(16, 8, 4)
 
-template <typename T, int LX, int TY, int S, bool SC>
+template <typename T, int LX, int TY, int S>
 static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,
                               const int2* items, int n_items, int* counter, const Scales& sc, int* err, int ctas,
                               cudaStream_t s) {
     using L = TmaLayout<T, LX, TY, S>;
-    auto kern = tma_batch_kernel<T, LX, TY, S, SC>;
+    auto kern = tma_batch_kernel<T, LX, TY, S>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
@@ -96,12 +95,10 @@ template <typename T>
 static cudaError_t batch_t(const TmaConfig& c, bool scaled, bool query, int* bps, const BatchGridDev* grids,
                            const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
                            int* err, int ctas, cudaStream_t s) {
-#define PW_BD(LX_, TY_, S_)                                                                                      \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                            \
-        return scaled ? batch_inst<T, LX_, TY_, S_, true>(query, bps, grids, maps, items, n_items, counter, sc, err, \
-                                                          ctas, s)                                               \
-                      : batch_inst<T, LX_, TY_, S_, false>(query, bps, grids, maps, items, n_items, counter, sc,     \
-                                                           err, ctas, s);
+    (void)scaled;   // the k-march folds the storage scales into its coefficients
+#define PW_BD(LX_, TY_, S_)                                                                                \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                      \
+        return batch_inst<T, LX_, TY_, S_>(query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
     PW_BATCH_CONFIGS(PW_BD)
 #undef PW_BD
     return cudaErrorInvalidConfiguration;

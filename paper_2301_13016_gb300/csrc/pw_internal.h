@@ -30,6 +30,32 @@ struct CoefDev {
     const float* tz;
 };
 
+// The scheme's coefficients with the storage scales folded in, per output
+// field (su, sv, sw).  Every term of the scheme is c * a * (b + d) with b and d
+// of one field, so on stored values (physical = stored * in) the term is
+// (c * in_a * in_b * out) * a~ * (b~ + d~) with out the output's scale: the
+// x terms pair u values, the y terms v values, the z terms w values, hence
+//   kx[f] = tcx * in_u * a_f,  ky[f] = tcy * in_v * a_f,  kz[f] = in_w * a_f,
+// a_f = in_f * out_f (kz multiplies the per-level tz coefficients).  With
+// power-of-two scales this is exact: the k-march then computes on stored
+// values directly, bit for bit what it computed on dequantised ones.
+struct FoldedCoef {
+    float kx[3], ky[3], kz[3];
+    const float* tz;   // tzc1 | tzc2 | tzd1 | tzd2, nz+2 each
+};
+
+__host__ __device__ inline FoldedCoef fold_coef(const CoefDev& cf, const Scales& sc) {
+    FoldedCoef k;
+    for (int f = 0; f < 3; ++f) {
+        const float a = sc.in[f] * sc.out[f];
+        k.kx[f] = cf.tcx * sc.in[0] * a;
+        k.ky[f] = cf.tcy * sc.in[1] * a;
+        k.kz[f] = sc.in[2] * a;
+    }
+    k.tz = cf.tz;
+    return k;
+}
+
 // Launch shape of the TMA k-march kernel.
 struct TmaConfig {
     int lx;      // lanes per row: 32 (tile 128 columns wide) or 16 (64 columns)

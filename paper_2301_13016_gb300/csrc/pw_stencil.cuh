@@ -308,8 +308,7 @@ enum { F_U = 0, F_V = 1, F_W = 2 };
 template <int NC, int LX, typename V, class Row, class Edge, class Out>
 __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row, const Edge& edge, const Out& out,
                                             const int xl, const bool first, const bool have_up, const bool compute,
-                                            const float tcx_, const float tcy_, const float* __restrict__ tz,
-                                            const int kk, const int nzp2) {
+                                            const FoldedCoef& k, const int kk, const int nzp2) {
     using O = VOps<V>;
     // x-neighbours of a row vector: value at x = -1 (m) and x = NC (p)
     auto nbr_m = [&](const V (&x)[NC], V e) { return O::sel(xl == 0, e, O::shfl_up(x[NC - 1], LX)); };
@@ -354,7 +353,9 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 #pragma unroll
     for (int c = 0; c < NC; ++c) ru[c] = rv[c] = rw[c] = O::zero();
     if (compute) {
-        const V tcx = O::splat(tcx_), tcy = O::splat(tcy_);
+        // per output field: x, y and lower vertical coefficients (storage scales folded in)
+        const V kxu = O::splat(k.kx[0]), kxv = O::splat(k.kx[1]), kxw = O::splat(k.kx[2]);
+        const V kyu = O::splat(k.ky[0]), kyv = O::splat(k.ky[1]), kyw = O::splat(k.ky[2]);
         V us[NC], un[NC], vn[NC], ws[NC];
         row(F_U, 0, -1, us);
         row(F_U, 0, 1, un);
@@ -397,33 +398,36 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
             pxv[c] = O::add(Vv[c + 1], Vv[c + 2]);   // v(j,i) + v(j,i+1)
             pys[c] = O::add(VS[c], VS[c + 1]);       // v(j-1,i) + v(j-1,i+1)
         }
-        const V tz1 = O::splat(__ldg(tz + kk));
+        const float t1 = __ldg(k.tz + kk);
+        const V tz1u = O::splat(t1 * k.kz[0]), tz1v = O::splat(t1 * k.kz[1]);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             // su
-            V x = O::mul(tcx, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
-            x = O::fma(tcy, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
-            ru[c] = O::fma(tz1, st.pdu[c], x);
+            V x = O::mul(kxu, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
+            x = O::fma(kyu, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
+            ru[c] = O::fma(tz1u, st.pdu[c], x);
             // sv
-            V y = O::mul(tcx, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
-            y = O::fma(tcy,
+            V y = O::mul(kxv, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
+            y = O::fma(kyv,
                        O::fma(O::neg(vn[c]), O::add(Vv[c + 1], vn[c]), O::mul(st.vs[c], O::add(Vv[c + 1], st.vs[c]))),
                        y);
-            rv[c] = O::fma(tz1, st.pdv[c], y);
+            rv[c] = O::fma(tz1v, st.pdv[c], y);
         }
         if (have_up) {   // kk < nz: upper vertical fluxes and sw
-            const V ntz2 = O::splat(-__ldg(tz + nzp2 + kk));
-            const V td1 = O::splat(__ldg(tz + 2 * nzp2 + kk));
-            const V ntd2 = O::splat(-__ldg(tz + 3 * nzp2 + kk));
+            const float t2 = __ldg(k.tz + nzp2 + kk);
+            const float d1 = __ldg(k.tz + 2 * nzp2 + kk);
+            const float d2 = __ldg(k.tz + 3 * nzp2 + kk);
+            const V ntz2u = O::splat(-(t2 * k.kz[0])), ntz2v = O::splat(-(t2 * k.kz[1]));
+            const V td1w = O::splat(d1 * k.kz[2]), ntd2w = O::splat(-(d2 * k.kz[2]));
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                ru[c] = O::fma(ntz2, O::mul(uu[c], pzu_n[c]), ru[c]);
-                rv[c] = O::fma(ntz2, O::mul(vu[c], pzv_n[c]), rv[c]);
-                V z = O::mul(tcx, O::fma(O::neg(W[c + 2]), rx[c + 1], O::mul(W[c], rx[c])));
-                z = O::fma(tcy, O::fma(O::neg(wn[c]), O::add(Vv[c + 1], vu[c]), O::mul(ws[c], O::add(st.vs[c], vus[c]))),
+                ru[c] = O::fma(ntz2u, O::mul(uu[c], pzu_n[c]), ru[c]);
+                rv[c] = O::fma(ntz2v, O::mul(vu[c], pzv_n[c]), rv[c]);
+                V z = O::mul(kxw, O::fma(O::neg(W[c + 2]), rx[c + 1], O::mul(W[c], rx[c])));
+                z = O::fma(kyw, O::fma(O::neg(wn[c]), O::add(Vv[c + 1], vu[c]), O::mul(ws[c], O::add(st.vs[c], vus[c]))),
                            z);
-                z = O::fma(td1, st.pdw[c], z);
-                rw[c] = O::fma(ntd2, O::mul(wu[c], pzw_n[c]), z);
+                z = O::fma(td1w, st.pdw[c], z);
+                rw[c] = O::fma(ntd2w, O::mul(wu[c], pzw_n[c]), z);
             }
         }
     }
@@ -566,13 +570,12 @@ struct MarchSmem {
 // `ring` counts the planes this CTA issued before; it is advanced by the
 // planes of this tile.  Returns false if a wait timed out (the error is
 // recorded and the copies in flight are drained).
-template <typename T, int LX, int TY, int S, bool SCALED, int MODE, int NC = 4, int RP = 1>
+template <typename T, int LX, int TY, int S, int MODE, int NC = 4, int RP = 1>
 __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>& sm, const CUtensorMap* tm_u,
                                            const CUtensorMap* tm_v, const CUtensorMap* tm_w, T* __restrict__ o0,
                                            T* __restrict__ o1, T* __restrict__ o2, const GridDev& g, const int ox,
-                                           const Scales& sc, const CoefDev& cf, const float dt, const int bx,
-                                           const int by, const int kb, const int ke, uint32_t& ring,
-                                           int* __restrict__ err) {
+                                           const FoldedCoef& kc, const float dt, const int bx, const int by,
+                                           const int kb, const int ke, uint32_t& ring, int* __restrict__ err) {
     using L = TmaLayout<T, LX, TY, S, NC, RP>;
     using V = typename std::conditional<RP == 1, float, float2>::type;
     constexpr int BW = L::BW;
@@ -627,21 +630,12 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
     const bool valid = (j <= g.ny) && (i0 <= g.nx);
     const bool valid2 = (j + 1 <= g.ny) && (i0 <= g.nx);   // the second row (RP = 2)
     const long long row_off = g.origin + (long long)j * g.pj + i0;
-    const float tcx = cf.tcx, tcy = cf.tcy;
+    // the arithmetic runs on stored values, the storage scales folded into the
+    // coefficients kc
     const int nzp2 = nz + 2;
     const unsigned FULL = 0xffffffffu;
-    auto ld = [&](const T* p, float (&o)[NC], float s) {
-        loadv<NC>(p, o);
-        if (SCALED) {
-#pragma unroll
-            for (int q = 0; q < NC; ++q) o[q] *= s;
-        }
-    };
-    auto ld1 = [&](const T* p, float s) {
-        float x = Store<T>::to_f(*p);
-        return SCALED ? x * s : x;
-    };
-    const float s_in[3] = {sc.in[0], sc.in[1], sc.in[2]};
+    auto ld = [&](const T* p, float (&o)[NC]) { loadv<NC>(p, o); };
+    auto ld1 = [&](const T* p) { return Store<T>::to_f(*p); };
 
     MarchRegs<NC, V> st;
     st.zero();
@@ -653,11 +647,11 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
     auto rowld = [&](int f, int up, int dr, V (&o)[NC]) {
         const T* P = stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + c0;
         if constexpr (RP == 1) {
-            ld(P, o, s_in[f]);
+            ld(P, o);
         } else {
             float a[NC], b[NC];
-            ld(P, a, s_in[f]);
-            ld(P + BW, b, s_in[f]);
+            ld(P, a);
+            ld(P + BW, b);
 #pragma unroll
             for (int q = 0; q < NC; ++q) o[q] = make_float2(a[q], b[q]);
         }
@@ -665,9 +659,9 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
     auto edgeld = [&](int f, int up, int dr) -> V {
         const T* P = stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + ce;
         if constexpr (RP == 1)
-            return ld1(P, s_in[f]);
+            return ld1(P);
         else
-            return make_float2(ld1(P, s_in[f]), ld1(P + BW, s_in[f]));
+            return make_float2(ld1(P), ld1(P + BW));
     };
 
     // One level of the march.  Returns false on abort.
@@ -702,11 +696,6 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
                         b[c] = comp(rv[c]);
                         d[c] = comp(rw[c]);
                     }
-                    if (SCALED) {
-                        a[c] *= sc.out[0];
-                        b[c] *= sc.out[1];
-                        d[c] *= sc.out[2];
-                    }
                 }
                 Epilogue<T, MODE>::template storevec<NC>(o0, o1, o2,
                                                          row_off + (long long)half * g.pj + (long long)kk * g.pk, a,
@@ -718,8 +707,8 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
                 if (valid) out_row(ru, rv, rw, u0, v0, w0, 0);
                 if (RP == 2 && valid2) out_row(ru, rv, rw, u0, v0, w0, 1);
             };
-            march_level<NC, LX>(st, rowld, edgeld, out, xl, lp == 0, have_up, (kk >= kb) && (kk >= 2), tcx, tcy,
-                                cf.tz, kk, nzp2);
+            march_level<NC, LX>(st, rowld, edgeld, out, xl, lp == 0, have_up, (kk >= kb) && (kk >= 2), kc, kk,
+                                nzp2);
         }
 #if PW_MARCH_SPLIT_ARRIVE
         // this warp is done with the plane of level kk; the last warp to say
@@ -786,13 +775,13 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
 }
 
 // One grid, one tile per CTA: blockIdx = (tile column, tile row, k segment).
-template <typename T, int LX, int TY, int S, bool SCALED, int MODE, int NC, int RP>
+template <typename T, int LX, int TY, int S, int MODE, int NC, int RP>
 __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP>::THREADS,
                                   (tma_min_blocks<T, LX, TY, S, NC, RP>()))
     tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
                const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
-               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const int seg0, const Scales sc,
-               const CoefDev cf, const float dt, int* __restrict__ err) {
+               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const int seg0, const FoldedCoef kc,
+               const float dt, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MarchSmem<T, LX, TY, S, NC, RP> sm(smem_raw);
     const int bz = seg0 + blockIdx.z;
@@ -801,7 +790,7 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP>::THREADS,
     if (ke < kb) return;   // empty k segment (the host never launches one)
     sm.init(threadIdx.y * 32 + threadIdx.x);
     uint32_t ring = 0;
-    march_tile<T, LX, TY, S, SCALED, MODE, NC, RP>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, sc, cf, dt,
+    march_tile<T, LX, TY, S, MODE, NC, RP>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, kc, dt,
                                                    blockIdx.x, blockIdx.y, kb, ke, ring, err);
 }
 
@@ -817,7 +806,7 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP>::THREADS,
 template <typename T, int NC, int RP>
 constexpr bool nc_ok() { return (NC == 4 && RP == 1) || sizeof(T) == 2; }
 
-template <typename T, int LX, int TY, int S, bool SC, int MODE, int NC, int RP>
+template <typename T, int LX, int TY, int S, int MODE, int NC, int RP>
 static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1,
                                    void* o2, const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
                                    int seg0, int seg_count, cudaStream_t s) {
@@ -825,14 +814,14 @@ static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* 
     return cudaErrorInvalidConfiguration;
   } else {
     using L = TmaLayout<T, LX, TY, S, NC, RP>;
-    auto kern = tma_kernel<T, LX, TY, S, SC, MODE, NC, RP>;
+    auto kern = tma_kernel<T, LX, TY, S, MODE, NC, RP>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (seg_count <= 0) seg_count = nseg - seg0;
     dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, seg_count);
     dim3 block(32, L::WARPS);
-    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, seg0, sc, cf,
-                                      dt, err);
+    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, seg0,
+                                      fold_coef(cf, sc), dt, err);
     return cudaGetLastError();
   }
 }
@@ -841,13 +830,11 @@ template <typename T, int MODE>
 static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                    const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
                                    const TmaConfig& c, cudaStream_t s) {
+    (void)scaled;   // the k-march folds the scales into its coefficients whatever they are
 #define PW_DISPATCH(LX_, TY_, S_, NC_, RP_)                                                                   \
     if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_)                           \
-        return scaled ? launch_tma_inst<T, LX_, TY_, S_, true, MODE, NC_, RP_>(g, ox, maps, o0, o1, o2, sc, cf, dt, \
-                                                                               err, c.nseg, c.seg0, c.seg_count, s) \
-                      : launch_tma_inst<T, LX_, TY_, S_, false, MODE, NC_, RP_>(g, ox, maps, o0, o1, o2, sc, cf,  \
-                                                                                dt, err, c.nseg, c.seg0,        \
-                                                                                c.seg_count, s);
+        return launch_tma_inst<T, LX_, TY_, S_, MODE, NC_, RP_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, \
+                                                                c.seg0, c.seg_count, s);
     PW_TMA_CONFIGS(PW_DISPATCH)
 #undef PW_DISPATCH
     return cudaErrorInvalidConfiguration;

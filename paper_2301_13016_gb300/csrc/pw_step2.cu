@@ -71,11 +71,11 @@ constexpr int tb2_min_blocks() {
     return m < 1 ? 1 : (m > MINB ? MINB : m);
 }
 
-template <typename T, int TY, int S, int MINB, bool SCALED>
+template <typename T, int TY, int S, int MINB>
 __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<T, TY, S, MINB>()))
     tb2_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
                const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
-               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const Scales sc, const CoefDev cf,
+               T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const FoldedCoef kc,
                const float dt, int* __restrict__ err) {
     using L = Tb2Layout<T, TY, S>;
     constexpr int NC = L::NC;
@@ -133,22 +133,18 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
     const int i0 = L::OX * bx + 1 + NC * (lane - 1);
     const bool valid = stage2 && lane >= 1 && lane <= 30 && j <= g.ny && i0 <= g.nx;
     const long long row_off = g.origin + (long long)j * g.pj + i0;
-    const float tcx = cf.tcx, tcy = cf.tcy;
+    // both stages run on stored values with the storage scales folded into the
+    // coefficients kc (a step stores its state with the scale it read it with,
+    // so q1 in shared memory is in stored units too)
     const int nzp2 = nz + 2;
     const unsigned FULL = 0xffffffffu;
-    const float s_in[3] = {sc.in[0], sc.in[1], sc.in[2]};
 
     int lp = 0;   // plane index (from pb) of the stage-1 level
     auto rowld1 = [&](int f, int up, int dr, float (&o)[NC]) {
         loadv<NC>(stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * L::BW + c0, o);
-        if (SCALED) {
-#pragma unroll
-            for (int q = 0; q < NC; ++q) o[q] *= s_in[f];
-        }
     };
     auto edgeld1 = [&](int f, int up, int dr) {
-        const float x = Store<T>::to_f(stages[slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * L::BW + ce]);
-        return SCALED ? x * s_in[f] : x;
+        return Store<T>::to_f(stages[slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * L::BW + ce]);
     };
     int m2 = 0;   // stage-2 level
     auto rowld2 = [&](int f, int up, int dr, float (&o)[NC]) {
@@ -191,8 +187,8 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                     *reinterpret_cast<float4*>(Q + 2 * L::QF) = make_float4(
                         fmaf(dt, rw[0], w0[0]), fmaf(dt, rw[1], w0[1]), fmaf(dt, rw[2], w0[2]), fmaf(dt, rw[3], w0[3]));
                 };
-                march_level<NC, 32>(st1, rowld1, edgeld1, out1, lane, lp == 0, have_up, (t >= kb1) && (t >= 2), tcx,
-                                    tcy, cf.tz, t, nzp2);
+                march_level<NC, 32>(st1, rowld1, edgeld1, out1, lane, lp == 0, have_up, (t >= kb1) && (t >= 2), kc,
+                                    t, nzp2);
             }
         }
         __syncthreads();   // q1(t) visible; the q0 slot of plane t is free
@@ -217,11 +213,6 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                     a[c] = fmaf(dt, ru[c], u1[c]);
                     b[c] = fmaf(dt, rv[c], v1[c]);
                     d[c] = fmaf(dt, rw[c], w1[c]);
-                    if (SCALED) {
-                        a[c] *= sc.out[0];
-                        b[c] *= sc.out[1];
-                        d[c] *= sc.out[2];
-                    }
                 }
                 const long long o = row_off + (long long)m * g.pk;
                 storev<NC>(o0 + o, a);
@@ -229,8 +220,8 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                 storev<NC>(o2 + o, d);
                 StepImages::vec<T, NC>(o0, o1, o2, o, a, b, d, g, j, i0);
             };
-            march_level<NC, 32>(st2, rowld2, edgeld2, out2, lane, m == kb1, m + 1 <= ke1, (m >= kb) && (m >= 2),
-                                tcx, tcy, cf.tz, m, nzp2);
+            march_level<NC, 32>(st2, rowld2, edgeld2, out2, lane, m == kb1, m + 1 <= ke1, (m >= kb) && (m >= 2), kc,
+                                m, nzp2);
         }
     }
 
@@ -245,18 +236,18 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
 // Instantiated (rows per CTA, stages, register budget in resident CTAs).
 #define PW_TB2_CONFIGS(X) X(8, 3, 1) X(8, 3, 2) X(8, 4, 1) X(12, 3, 1) X(16, 3, 1) X(16, 4, 1)
 
-template <typename T, int TY, int S, int MINB, bool SC>
+template <typename T, int TY, int S, int MINB>
 static cudaError_t launch_tb2_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                    const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
                                    cudaStream_t s) {
     using L = Tb2Layout<T, TY, S>;
-    auto kern = tb2_kernel<T, TY, S, MINB, SC>;
+    auto kern = tb2_kernel<T, TY, S, MINB>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + L::OX - 1) / L::OX, (g.ny + L::OY - 1) / L::OY, nseg);
     dim3 block(32, TY);
-    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg, sc, cf, dt,
-                                      err);
+    kern<<<grid, block, L::SMEM, s>>>(maps[0], maps[1], maps[2], (T*)o0, (T*)o1, (T*)o2, g, ox, nseg,
+                                      fold_coef(cf, sc), dt, err);
     return cudaGetLastError();
 }
 
@@ -264,10 +255,10 @@ template <typename T>
 static cudaError_t launch_tb2_t(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                 const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
                                 const Step2Config& c, cudaStream_t s) {
-#define PW_DISPATCH(TY_, S_, M_)                                                                                 \
-    if (c.ty == TY_ && c.stages == S_ && c.minb == M_)                                                           \
-        return scaled ? launch_tb2_inst<T, TY_, S_, M_, true>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s)  \
-                      : launch_tb2_inst<T, TY_, S_, M_, false>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s);
+    (void)scaled;   // the k-march folds the storage scales into its coefficients
+#define PW_DISPATCH(TY_, S_, M_)                                                                             \
+    if (c.ty == TY_ && c.stages == S_ && c.minb == M_)                                                       \
+        return launch_tb2_inst<T, TY_, S_, M_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s);
     PW_TB2_CONFIGS(PW_DISPATCH)
 #undef PW_DISPATCH
     return cudaErrorInvalidConfiguration;
@@ -286,7 +277,7 @@ template <typename T>
 static int tb2_blocks_t(const Step2Config& c) {
 #define PW_OCC(TY_, S_, M_)                                                                                    \
     if (c.ty == TY_ && c.stages == S_ && c.minb == M_) {                                                       \
-        auto kern = tb2_kernel<T, TY_, S_, M_, false>;                                                           \
+        auto kern = tb2_kernel<T, TY_, S_, M_>;                                                                  \
         if (set_smem_attr_once(kern, (int)Tb2Layout<T, TY_, S_>::SMEM) != cudaSuccess) return 0;               \
         int n = 0;                                                                                             \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * TY_, Tb2Layout<T, TY_, S_>::SMEM) !=  \

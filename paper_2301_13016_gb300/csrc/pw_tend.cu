@@ -66,7 +66,7 @@ static int blocks_per_sm_t(const TmaConfig& c) {
 #define PW_OCC(LX_, TY_, S_, NC_, RP_)                                                                 \
     if constexpr (nc_ok<T, NC_, RP_>())                                                                \
         if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_) {              \
-            auto kern = tma_kernel<T, LX_, TY_, S_, false, MODE_TEND, NC_, RP_>;                       \
+            auto kern = tma_kernel<T, LX_, TY_, S_, MODE_TEND, NC_, RP_>;                              \
             using L = TmaLayout<T, LX_, TY_, S_, NC_, RP_>;                                            \
             if (set_smem_attr_once(kern, (int)L::SMEM) != cudaSuccess) return 0;                       \
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, L::THREADS, L::SMEM) != cudaSuccess) \
