@@ -200,3 +200,28 @@ def test_automatic_launch_shapes():
     assert h.tma_config() == dict(f32, ty=8, nseg=h.tma_config()["nseg"])
     h.set_tma_config()
     assert pick(pwlib.Grid(256, 64, 8, dtype="bf16")) == {k: v for k, v in h.tma_config().items() if k != "nseg"}
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_host_path_16bit_matches_device_path(dtype):
+    """pw_tendencies_host with 16-bit storage (the packed two-row shape,
+    pipelined in 8-level chunks; FP16 with scales) gives the device path's
+    bits."""
+    nx, ny, nz = 256, 20, 64
+    c = inputs.make_coeffs(nz)
+    f = inputs.random_fields(nx, ny, nz)
+    sc = precision.suggest_scales([float(x.abs().max()) for x in f], c, dtype)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype)
+    h = pwlib.PW(g, c)
+    dev = [g.from_dense(x, scale=s) for x, s in zip(f, sc[:3])]
+    outs = [g.alloc(fill=NAN) for _ in range(3)]
+    h.tendencies(*dev, *outs, scale=sc)
+    h.sync()
+    hin = [t.cpu().pin_memory() for t in dev]
+    hout = [torch.zeros(g.alloc_elems, dtype=g.torch_dtype).pin_memory() for _ in range(3)]
+    h.tendencies_host(*hin, *hout, scale=sc)
+    assert h.last_kernel == 2
+    for o, t in zip(outs, hout):
+        a = g.view(o)[1:-1, 1:-1, 1:-1].contiguous().view(torch.int16).cpu()
+        b = g.view(t)[1:-1, 1:-1, 1:-1].contiguous().view(torch.int16)
+        assert torch.equal(a, b)
