@@ -168,16 +168,12 @@ static pw_status_t encode_map_box(pw_handle_t h, const void* ptr, int box_w, int
     return PW_OK;
 }
 
-// Tensor map for the single-step k-march shape (lx lanes x nc cells, ty rows).
-static pw_status_t encode_map(pw_handle_t h, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
-                              int nc = 4) {
-    (void)ox;
+// Tensor map for the single-grid k-march shape (lx lanes x nc cells, ty rows).
+static pw_status_t encode_map(pw_handle_t h, const void* ptr, int lx, int ty, CUtensorMap* out, int nc = 4) {
     return encode_map_box(h, ptr, tma_box_width(h->grid.dtype, lx, nc), ty + 2, out);
 }
 
-pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
-                                  int nc) {
-    (void)ox;
+pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int lx, int ty, CUtensorMap* out, int nc) {
     return encode_tensor_map_box(g, ptr, tma_box_width(g.dtype, lx, nc), ty + 2, out);
 }
 
@@ -512,10 +508,10 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         TmaConfig c = choose_tma(h, false);
         CUtensorMap maps[3];
         for (int q = 0; q < 3; ++q) {
-            pw_status_t st = encode_map(h, ins[q], ox, c.lx, c.ty, &maps[q], c.nc);
+            pw_status_t st = encode_map(h, ins[q], c.lx, c.ty, &maps[q], c.nc);
             if (st != PW_OK) return st;
         }
-        cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, scaled, cf, h->d_err, c, s);
+        cudaError_t e = launch_tend_tma(h->grid.dtype, g, ox, maps, su, sv, sw, sc, cf, h->d_err, c, s);
         if (e != cudaSuccess) return cuda_fail(e, "TMA tendency kernel launch");
         h->last_kernel = 2;
     } else {
@@ -598,7 +594,7 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
     cfg.seg_count = 1;
     CUtensorMap maps[3];
     for (int q = 0; q < 3; ++q) {
-        pw_status_t st = encode_map(h, h->d_stage[q], ox, cfg.lx, cfg.ty, &maps[q], cfg.nc);
+        pw_status_t st = encode_map(h, h->d_stage[q], cfg.lx, cfg.ty, &maps[q], cfg.nc);
         if (st != PW_OK) return st;
     }
     const GridDev gd = to_dev(g);
@@ -622,7 +618,7 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         PW_CUDA(cudaEventRecord(h->ev_in[c], h->hs[0]), "pipeline event");
         PW_CUDA(cudaStreamWaitEvent(h->hs[1], h->ev_in[c], 0), "pipeline wait");
         cfg.seg0 = c;
-        cudaError_t e = launch_tend_tma(g.dtype, gd, ox, maps, h->d_stage[3], h->d_stage[4], h->d_stage[5], sc, scaled,
+        cudaError_t e = launch_tend_tma(g.dtype, gd, ox, maps, h->d_stage[3], h->d_stage[4], h->d_stage[5], sc,
                                         cf, h->d_err, cfg, h->hs[1]);
         if (e != cudaSuccess) return cuda_fail(e, "TMA tendency kernel launch");
         PW_CUDA(cudaEventRecord(h->ev_comp[c], h->hs[1]), "pipeline event");
@@ -704,16 +700,16 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
                 pw_status_t st = encode_map_box(h, src[q], step2_box_width(), c2.ty + 2, &maps[q]);
                 if (st != PW_OK) return st;
             }
-            e = launch_step2_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c2, s);
+            e = launch_step2_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c2, s);
             done += 2;
             kind = 3;
         } else if (use_tma) {
             CUtensorMap maps[3];
             for (int q = 0; q < 3; ++q) {
-                pw_status_t st = encode_map(h, src[q], ox, c.lx, c.ty, &maps[q], c.nc);
+                pw_status_t st = encode_map(h, src[q], c.lx, c.ty, &maps[q], c.nc);
                 if (st != PW_OK) return st;
             }
-            e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, scaled, cf, dt, h->d_err, c, s);
+            e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c, s);
             done += 1;
             // the single-step k-march writes the images of a one-cell halo only
             for (int q = 0; q < 3 && e == cudaSuccess && g.halo != 1; ++q)
@@ -773,7 +769,7 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
         CUtensorMap maps[6];
         const int rows = adjoint_tma_rows();
         for (int q = 0; q < 6; ++q) {
-            pw_status_t st = encode_map(h, ins[q], ox, 32, rows, &maps[q]);
+            pw_status_t st = encode_map(h, ins[q], 32, rows, &maps[q]);
             if (st != PW_OK) return st;
         }
         const long long tiles = (long long)((g.nx + 127) / 128) * ((g.ny + rows - 1) / rows);

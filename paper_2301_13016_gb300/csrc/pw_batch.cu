@@ -92,10 +92,9 @@ static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, c
 }
 
 template <typename T>
-static cudaError_t batch_t(const TmaConfig& c, bool scaled, bool query, int* bps, const BatchGridDev* grids,
+static cudaError_t batch_t(const TmaConfig& c, bool query, int* bps, const BatchGridDev* grids,
                            const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
                            int* err, int ctas, cudaStream_t s) {
-    (void)scaled;   // the k-march folds the storage scales into its coefficients
 #define PW_BD(LX_, TY_, S_)                                                                                \
     if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                      \
         return batch_inst<T, LX_, TY_, S_>(query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
@@ -104,14 +103,14 @@ static cudaError_t batch_t(const TmaConfig& c, bool scaled, bool query, int* bps
     return cudaErrorInvalidConfiguration;
 }
 
-static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool scaled, bool query, int* bps,
+static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool query, int* bps,
                                   const BatchGridDev* grids, const CUtensorMap* maps, const int2* items, int n_items,
                                   int* counter, const Scales& sc, int* err, int ctas, cudaStream_t s) {
     switch (dt) {
-        case PW_F32: return batch_t<float>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+        case PW_F32: return batch_t<float>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
         case PW_BF16:
-            return batch_t<__nv_bfloat16>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
-        case PW_F16: return batch_t<__half>(c, scaled, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+            return batch_t<__nv_bfloat16>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+        case PW_F16: return batch_t<__half>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -152,7 +151,6 @@ struct pw_batch_s {
     std::vector<const void*> ptrs;   // 6n pointers the tables were built for
     bool tables_ok = false, items_ok = false;
     Scales graph_sc{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
-    bool graph_scaled = false;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -197,7 +195,7 @@ static pw_status_t build_items(pw_batch_t b) {
     if (e != cudaSuccess) return internal_cuda_fail(e, "batch work list upload");
     int bps = 0;
     Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
-    e = batch_dispatch(b->dtype, b->cfg, false, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
+    e = batch_dispatch(b->dtype, b->cfg, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
                        nullptr);
     if (e != cudaSuccess || bps < 1) return internal_cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
                                                                "batch kernel occupancy");
@@ -329,13 +327,11 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
     if (!u || !v || !w || !su || !sv || !sw) return bfail(PW_ERR_ARG, "a pointer table is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Scales sc;
-    bool scaled = false;
     for (int q = 0; q < 3; ++q) {
         sc.in[q] = scale ? scale[q] : 1.f;
         sc.out[q] = scale ? scale[3 + q] : 1.f;
         if (!(sc.in[q] > 0.f) || !(sc.out[q] > 0.f) || !(sc.in[q] < 3.0e38f) || !(sc.out[q] < 3.0e38f))
             return bfail(PW_ERR_ARG, "scales must be finite and > 0");
-        if (sc.in[q] != 1.f || sc.out[q] != 1.f) scaled = true;
     }
     // pointer tables: validate, and rebuild the device tables if they changed
     std::vector<const void*> p(6 * (size_t)b->n);
@@ -356,7 +352,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         for (int q = 0; q < b->n; ++q) {
             const pw_grid_t& g = b->grids[q];
             for (int a = 0; a < 3; ++a) {
-                pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->ox[q], b->cfg.lx, b->cfg.ty,
+                pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->cfg.lx, b->cfg.ty,
                                                    &b->h_maps[3 * (size_t)q + a]);
                 if (st != PW_OK) return st;
             }
@@ -385,14 +381,15 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         b->ptrs = p;
         b->tables_ok = true;
     }
-    // the graph: counter reset + persistent kernel, captured once per config
-    if (b->exec && (scaled != b->graph_scaled || (scaled && std::memcmp(&sc, &b->graph_sc, sizeof sc) != 0)))
+    // the graph: counter reset + persistent kernel, captured once per config and
+    // per set of scales (the kernel's folded coefficients are launch parameters)
+    if (b->exec && std::memcmp(&sc, &b->graph_sc, sizeof sc) != 0)
         drop_graph(b);
     if (!b->exec) {
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
         if (e == cudaSuccess)
-            e = batch_dispatch(b->dtype, b->cfg, scaled, false, nullptr, b->d_grids, b->d_maps, b->d_items,
+            e = batch_dispatch(b->dtype, b->cfg, false, nullptr, b->d_grids, b->d_maps, b->d_items,
                                (int)b->items.size(), b->d_counter, sc, b->d_err, b->ctas, b->cap);
         cudaGraph_t gr = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
@@ -405,7 +402,6 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         }
         b->graph = gr;
         b->graph_sc = sc;
-        b->graph_scaled = scaled;
     }
     cudaError_t e = cudaGraphLaunch(b->exec, s);
     if (e != cudaSuccess) return internal_cuda_fail(e, "batch graph launch");

@@ -89,7 +89,7 @@ bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c);
 size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c);
 
 cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps /*u,v,w*/,
-                            void* su, void* sv, void* sw, const Scales& sc, bool scaled, const CoefDev& cf,
+                            void* su, void* sv, void* sw, const Scales& sc, const CoefDev& cf,
                             int* err, const TmaConfig& c, cudaStream_t s);
 
 // Forward-Euler step kernels: (nu, nv, nw) = (u, v, w) + tstep * s(u, v, w),
@@ -98,14 +98,14 @@ cudaError_t launch_step_generic(pw_dtype_t dt, const GridDev& g, const void* u, 
                                 void* nu, void* nv, void* nw, const Scales& sc, bool scaled, const CoefDev& cf,
                                 float tstep, int num_sms, cudaStream_t s);
 cudaError_t launch_step_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
-                            void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                            void* nw, const Scales& sc, const CoefDev& cf, float tstep, int* err,
                             const TmaConfig& c, cudaStream_t s);
 
 // Two forward-Euler steps per pass (temporal blocking): (nu, nv, nw) = q2
 // with q1 = q + tstep*s(q), q2 = q1 + tstep*s(q1); needs a lateral halo of
 // at least 2 and maps encoded with box step2_box_width() x (ty + 2).
 cudaError_t launch_step2_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
-                             void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                             void* nw, const Scales& sc, const CoefDev& cf, float tstep, int* err,
                              const Step2Config& c, cudaStream_t s);
 bool step2_config_supported(const Step2Config& c);
 int step2_box_width();
@@ -151,8 +151,7 @@ bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
 pw_status_t validate_grid(const pw_grid_t* g);
 bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why);
 bool aligned16(const void* p);
-pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int ox, int lx, int ty, CUtensorMap* out,
-                              int nc = 4);
+pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int lx, int ty, CUtensorMap* out, int nc = 4);
 // Same with an explicit box (box_w elements along x, box_h rows).
 pw_status_t encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out);
 

@@ -450,7 +450,7 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 // ---------------------------------------------------------------------------
 // TMA k-march.
 //
-// A tile is TX = 4*LX interior columns by TY rows and one k segment; the CTA
+// A tile is NC*LX interior columns by TY*RP rows and one k segment; the CTA
 // marches up the column one level at a time.  Level planes of u, v, w (the
 // tile plus a one-cell halo, widened in x to the 16-byte TMA granule) arrive
 // in a ring of S shared-memory slots by 3D TMA box copies that one thread
@@ -828,9 +828,8 @@ static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* 
 
 template <typename T, int MODE>
 static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
-                                   const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
+                                   const Scales& sc, const CoefDev& cf, float dt, int* err,
                                    const TmaConfig& c, cudaStream_t s) {
-    (void)scaled;   // the k-march folds the scales into its coefficients whatever they are
 #define PW_DISPATCH(LX_, TY_, S_, NC_, RP_)                                                                   \
     if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_)                           \
         return launch_tma_inst<T, LX_, TY_, S_, MODE, NC_, RP_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, \

@@ -23,16 +23,16 @@ cudaError_t launch_step_generic(pw_dtype_t dt, const GridDev& g, const void* u, 
 }
 
 cudaError_t launch_step_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
-                            void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                            void* nw, const Scales& sc, const CoefDev& cf, float tstep, int* err,
                             const TmaConfig& c, cudaStream_t s) {
     switch (dt) {
         case PW_F32:
-            return launch_tma_mode<float, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c, s);
+            return launch_tma_mode<float, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c, s);
         case PW_BF16:
-            return launch_tma_mode<__nv_bfloat16, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c,
+            return launch_tma_mode<__nv_bfloat16, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c,
                                                              s);
         case PW_F16:
-            return launch_tma_mode<__half, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c, s);
+            return launch_tma_mode<__half, MODE_STEP>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -253,9 +253,8 @@ static cudaError_t launch_tb2_inst(const GridDev& g, int ox, const CUtensorMap* 
 
 template <typename T>
 static cudaError_t launch_tb2_t(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
-                                const Scales& sc, bool scaled, const CoefDev& cf, float dt, int* err,
+                                const Scales& sc, const CoefDev& cf, float dt, int* err,
                                 const Step2Config& c, cudaStream_t s) {
-    (void)scaled;   // the k-march folds the storage scales into its coefficients
 #define PW_DISPATCH(TY_, S_, M_)                                                                             \
     if (c.ty == TY_ && c.stages == S_ && c.minb == M_)                                                       \
         return launch_tb2_inst<T, TY_, S_, M_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, s);
@@ -306,13 +305,13 @@ int step2_blocks_per_sm(pw_dtype_t dt, const Step2Config& c) {
 }
 
 cudaError_t launch_step2_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* nu, void* nv,
-                             void* nw, const Scales& sc, bool scaled, const CoefDev& cf, float tstep, int* err,
+                             void* nw, const Scales& sc, const CoefDev& cf, float tstep, int* err,
                              const Step2Config& c, cudaStream_t s) {
     switch (dt) {
-        case PW_F32: return launch_tb2_t<float>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c, s);
+        case PW_F32: return launch_tb2_t<float>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c, s);
         case PW_BF16:
-            return launch_tb2_t<__nv_bfloat16>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c, s);
-        case PW_F16: return launch_tb2_t<__half>(g, ox, maps, nu, nv, nw, sc, scaled, cf, tstep, err, c, s);
+            return launch_tb2_t<__nv_bfloat16>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c, s);
+        case PW_F16: return launch_tb2_t<__half>(g, ox, maps, nu, nv, nw, sc, cf, tstep, err, c, s);
     }
     return cudaErrorInvalidValue;
 }

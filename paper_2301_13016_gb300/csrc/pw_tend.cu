@@ -21,13 +21,13 @@ cudaError_t launch_tend_generic(pw_dtype_t dt, const GridDev& g, const void* u, 
 }
 
 cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUtensorMap* maps, void* su, void* sv,
-                            void* sw, const Scales& sc, bool scaled, const CoefDev& cf, int* err,
+                            void* sw, const Scales& sc, const CoefDev& cf, int* err,
                             const TmaConfig& c, cudaStream_t s) {
     switch (dt) {
-        case PW_F32: return launch_tma_mode<float, MODE_TEND>(g, ox, maps, su, sv, sw, sc, scaled, cf, 0.f, err, c, s);
+        case PW_F32: return launch_tma_mode<float, MODE_TEND>(g, ox, maps, su, sv, sw, sc, cf, 0.f, err, c, s);
         case PW_BF16:
-            return launch_tma_mode<__nv_bfloat16, MODE_TEND>(g, ox, maps, su, sv, sw, sc, scaled, cf, 0.f, err, c, s);
-        case PW_F16: return launch_tma_mode<__half, MODE_TEND>(g, ox, maps, su, sv, sw, sc, scaled, cf, 0.f, err, c, s);
+            return launch_tma_mode<__nv_bfloat16, MODE_TEND>(g, ox, maps, su, sv, sw, sc, cf, 0.f, err, c, s);
+        case PW_F16: return launch_tma_mode<__half, MODE_TEND>(g, ox, maps, su, sv, sw, sc, cf, 0.f, err, c, s);
     }
     return cudaErrorInvalidValue;
 }
