@@ -217,6 +217,19 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
 pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void *tmp_v, void *tmp_w,
                     float dt, int32_t nsteps, const float *scale, pw_stream_t stream);
 
+/*
+ * One forward-Euler step out of place: (nu, nv, nw) = (u, v, w) + dt *
+ * s(u, v, w) on the interior levels 1..nz, plus the periodic images of the
+ * result in the lateral halo (doubly periodic domain), with the kernel one
+ * step of pw_step uses, so the bits equal those of pw_step(nsteps = 1).
+ * The inputs are not modified and their lateral halos must already hold
+ * periodic images (as pw_step, pw_step_to and pw_fill_halo_periodic leave
+ * them).  scale as in pw_step.  The six pointers must be distinct.
+ * pw_last_kernel reports 1 (generic) or 2 (TMA).
+ */
+pw_status_t pw_step_to(pw_handle_t h, const void *u, const void *v, const void *w, void *nu, void *nv, void *nw,
+                       float dt, const float *scale, pw_stream_t stream);
+
 /* Flags of pw_adjoint. */
 #define PW_ADJ_ACCUMULATE 1  /* g += alpha * J^T l                        */
 #define PW_ADJ_PERIODIC   2  /* doubly periodic domain (see pw_adjoint)    */
@@ -254,6 +267,21 @@ pw_status_t pw_step(pw_handle_t h, void *u, void *v, void *w, void *tmp_u, void 
 pw_status_t pw_adjoint(pw_handle_t h, const void *u, const void *v, const void *w,
                        const void *lsu, const void *lsv, const void *lsw,
                        void *gu, void *gv, void *gw, float alpha, int32_t flags, pw_stream_t stream);
+
+/*
+ * Launch shape of the TMA adjoint on this handle (0 = automatic, field by
+ * field): cells = consecutive cells a thread owns along x (a CTA covers
+ * 32*cells columns), ty = rows per CTA (one warp each), stages = ring slots
+ * of the six planes (levels k-1, k, k+1 resident, the rest in flight), nseg =
+ * CTAs along z (1..nz; automatic: the count that best fills the last wave of
+ * CTAs, segments of >= 8 levels).  Instantiated (cells, ty, stages): (4,5,4)
+ * (4,4,4) (4,6,4) (2,4,4) (2,5,4) (2,6,4) (2,8,4) (2,8,3); others give
+ * PW_ERR_UNSUPPORTED, a negative value or nseg > nz PW_ERR_ARG.  Each cell's
+ * arithmetic is the same in every shape.  pw_get_adjoint_config: out =
+ * {cells, ty, stages, nseg} that the next TMA adjoint call will use.
+ */
+pw_status_t pw_set_adjoint_config(pw_handle_t h, int32_t cells, int32_t ty, int32_t stages, int32_t nseg);
+pw_status_t pw_get_adjoint_config(pw_handle_t h, int32_t out[4]);
 
 /*
  * Periodic lateral boundary: copy interior values into the lateral halo of

@@ -1,13 +1,15 @@
 """torch.autograd over forward-Euler rollouts of the PW advection system.
 
 PWRollout.apply(u, v, w, handle, dt, nsteps, checkpoint_every) runs nsteps
-fused Euler steps (pw_step) from the state (u, v, w) (flat allocations of the
+forward-Euler steps from the state (u, v, w) (flat allocations of the
 handle's FP32 grid; interior values are the state, halos are refreshed) and
-returns the final state as new allocations.  Backward runs the reverse sweep
-g_n = g_{n+1} + dt * F^T J(q_n)^T g_{n+1} (pw_adjoint with PW_ADJ_PERIODIC |
-PW_ADJ_ADD_LAMBDA), recomputing the states of each checkpoint segment from
-its stored start state: memory holds one state per checkpoint plus one
-segment, not every step.
+returns the final state as new allocations.  Each step is one out-of-place
+pass (pw_step_to), so a state, once written, is never modified: the
+checkpoints are the states themselves, kept by reference.  Backward runs the
+reverse sweep g_n = g_{n+1} + dt * F^T J(q_n)^T g_{n+1} (pw_adjoint with
+PW_ADJ_PERIODIC | PW_ADJ_ADD_LAMBDA), recomputing the states of each
+checkpoint segment from its start state: memory holds one state per
+checkpoint plus one segment, not every step.
 
 Gradients flow through interior values: the gradient returned for u, v, w
 is zero on halo entries (they are copies of interior values), and the halo
@@ -24,6 +26,13 @@ def _interior_mask(grid, device):
     return m
 
 
+def _new_state(grid, device, fill=None):
+    """Three fields for a state that a step pass writes: levels 1..nz with
+    their lateral halos (the z-halo planes and the padding are never read;
+    they are left unset inside the sweep and zeroed for a returned state)."""
+    return [grid.alloc(device=device, fill=fill) for _ in range(3)]
+
+
 class PWRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u, v, w, handle, dt, nsteps, checkpoint_every=5):
@@ -32,15 +41,17 @@ class PWRollout(torch.autograd.Function):
             raise ValueError("PWRollout needs an FP32 grid")
         every = max(1, int(checkpoint_every))
         state = [t.detach().clone() for t in (u, v, w)]
-        tmp = [grid.alloc(device=u.device, fill=None) for _ in range(3)]
+        for t in state:                              # periodic halos of the start state
+            handle.fill_halo_periodic(t)
         ckpts = []
-        n = 0
-        handle.step(*state, *tmp, dt, 0)           # refresh halos of the start state
-        while n < nsteps:
-            ckpts.append([t.clone() for t in state])
-            m = min(every, nsteps - n)
-            handle.step(*state, *tmp, dt, m)
-            n += m
+        for n in range(int(nsteps)):
+            if n % every == 0:
+                ckpts.append(state)
+            nxt = _new_state(grid, u.device, fill=0.0 if n == nsteps - 1 else None)
+            handle.step_to(*state, *nxt, dt)
+            state = nxt
+        if not ckpts:                                # nsteps = 0: the result is a copy of the start state
+            state = [t.clone() for t in state]
         ctx.handle, ctx.dt, ctx.nsteps, ctx.every = handle, float(dt), int(nsteps), every
         ctx.save_for_backward(*[t for c in ckpts for t in c])
         return tuple(state)
@@ -55,27 +66,24 @@ class PWRollout(torch.autograd.Function):
         mask = _interior_mask(grid, dev)
         g = []
         for x in (gu, gv, gw):
-            y = torch.zeros(grid.alloc_elems, dtype=torch.float32, device=dev)
-            if x is not None:
-                y[mask] = x.to(torch.float32)[mask]
-            g.append(y)
-        g2 = [torch.zeros_like(t) for t in g]
-        tmp = [grid.alloc(device=dev, fill=None) for _ in range(3)]
+            g.append(torch.where(mask, x.to(torch.float32), 0.0) if x is not None
+                     else torch.zeros(grid.alloc_elems, dtype=torch.float32, device=dev))
+        g2 = [torch.empty_like(t) for t in g]   # the adjoint writes every interior cell
         for s in range(len(ckpts) - 1, -1, -1):
             n0 = s * every
             m = min(every, nsteps - n0)
             # recompute the states q_{n0} .. q_{n0+m-1} of this segment
-            states = [[t.clone() for t in ckpts[s]]]
+            states = [list(ckpts[s])]
             for _ in range(m - 1):
-                nxt = [t.clone() for t in states[-1]]
-                h.step(*nxt, *tmp, dt, 1)
+                nxt = _new_state(grid, dev)
+                h.step_to(*states[-1], *nxt, dt)
                 states.append(nxt)
             for q in reversed(states):
                 h.adjoint(*q, *g, *g2, alpha=dt, flags=PW_ADJ_PERIODIC | PW_ADJ_ADD_LAMBDA)
                 g, g2 = g2, g
             del states
         for t in g:
-            t[~mask] = 0.0
+            t.masked_fill_(~mask, 0.0)
         return g[0], g[1], g[2], None, None, None, None
 
 

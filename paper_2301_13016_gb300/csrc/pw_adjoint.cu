@@ -164,19 +164,20 @@ __global__ void adjoint_gather_kernel(const GridDev g, const AdjArgs a, const Co
 }
 
 // ---------------------------------------------------------------------------
-// TMA k-march adjoint (periodic mode, FP32).  A CTA owns 128 x TY interior
-// columns; one thread issues 3D TMA copies of the u, v, w and lsu, lsv, lsw
-// planes (tile plus one-cell halo) into a ring of S slots, keeping levels
-// k-1, k, k+1 resident while S-3 more are in flight.  The halos of u, v, w
-// and of l must hold periodic images.
-constexpr int kAdjTX = 128;
+// TMA k-march adjoint (periodic mode, FP32).  A CTA owns 32*NA columns x TY
+// rows of the interior (NA cells per thread); one thread issues 3D TMA copies
+// of the u, v, w and lsu, lsv, lsw planes (tile plus one-cell halo) into a
+// ring of S slots, keeping levels k-1, k, k+1 resident while S-3 more are in
+// flight.  The halos of u, v, w and of l must hold periodic images.
 constexpr int kAdjPAD = 4;                       // 16-byte granule of FP32
-constexpr int kAdjBW = kAdjTX + 2 * kAdjPAD;
 
-template <int TY, int S>
+template <int NA, int TY, int S>
 struct AdjLayout {
+    static_assert(NA == 2 || NA == 4, "2 or 4 cells per thread");
+    static constexpr int TX = 32 * NA;
+    static constexpr int BW = TX + 2 * kAdjPAD;
     static constexpr int ROWS = TY + 2;
-    static constexpr int FIELD_RAW = kAdjBW * ROWS;
+    static constexpr int FIELD_RAW = BW * ROWS;
     static constexpr int FIELD = ((FIELD_RAW * 4 + 127) / 128) * 32;   // floats, 128-byte multiple
     static constexpr int STAGE = 6 * FIELD;
     static constexpr uint32_t TX_BYTES = 6u * FIELD_RAW * 4u;
@@ -187,23 +188,64 @@ struct AdjMaps {
     CUtensorMap m[6];   // u, v, w, lsu, lsv, lsw
 };
 
+// NA consecutive floats at a 4*NA-byte aligned address
+// Build-time knob: load a level's vertical coefficients one level ahead (1)
+// or at the level (0).
+#ifndef PW_ADJ_PREFETCH
+#define PW_ADJ_PREFETCH 1
+#endif
+
+template <int NA>
+__device__ __forceinline__ void adj_ldv(const float* p, float (&o)[NA]) {
+    if constexpr (NA == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+}
+template <int NA>
+__device__ __forceinline__ void adj_stv(float* p, const float (&v)[NA]) {
+    if constexpr (NA == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+// CTAs per SM a shape's register budget is sized for: what shared memory
+// allows, at most 2 for 4 cells a thread (their gather needs 165-182
+// registers), and for 2 cells as many as leave each thread >= 96 registers
+// (the gather of 2 cells needs about that many without spilling).
+template <int NA, int TY, int S>
+constexpr int adj_min_blocks() {
+    constexpr int by_smem = (int)((227u * 1024u) / AdjLayout<NA, TY, S>::SMEM);
+    constexpr int cap = NA == 4 ? 2 : 65536 / (32 * TY * 96);
+    constexpr int m = by_smem < cap ? by_smem : cap;
+    return m < 1 ? 1 : m;
+}
+
 // ---------------------------------------------------------------------------
-// The gather kernel on that ring: a thread owns 4 consecutive cells of one
-// row, so each (field, level, row) it needs is one 16-byte shared load for
-// all 4 cells, and the x neighbours come from the adjacent lanes by warp
-// shuffles (the row's end lanes read theirs from the halo columns), as in
-// the forward k-march: 30 vector loads per level.  (Four cells 32 columns
+// The gather kernel on that ring: a thread owns NA consecutive cells of one
+// row, so each (field, level, row) it needs is one 16-byte (NA = 4) or
+// 8-byte (NA = 2) shared load for all of them, and the x neighbours come from
+// the adjacent lanes by warp shuffles (the row's end lanes read theirs from
+// the halo columns), as in the forward k-march: 30 vector loads per level.  (Four cells 32 columns
 // apart, read one word at a time, took about 200 scalar loads per level and
 // ran at 58 against 79 Gcell/s on GB300.)  Levels 3..nz-2 have every term and run without any masking; the
 // others select away the terms that do not exist there (a select, not a
 // multiplication by zero, so values read from a slot that holds another
 // level, or a sensitivity outside the scheme's outputs, never reach a sum).
-template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY, 2)
+template <int NA, int TY, int S>
+__global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
     adjoint_vec_kernel(const __grid_constant__ AdjMaps maps, float* __restrict__ gu, float* __restrict__ gv,
                        float* __restrict__ gw, const GridDev g, const int ox, const int nseg, const CoefDev cf,
                        const float alpha, const int accumulate, const int add_lambda, int* __restrict__ err) {
-    using L = AdjLayout<TY, S>;
+    using L = AdjLayout<NA, TY, S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* stages = reinterpret_cast<float*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * L::STAGE * 4);
@@ -215,7 +257,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
     const int ke = (int)(((long long)(blockIdx.z + 1) * nz) / nseg);
     if (ke < kb) return;
     const int pb = max(kb - 1, 1), pe = min(ke + 1, nz), np = pe - pb + 1;
-    const int X0 = ox + 1 + kAdjTX * blockIdx.x - kAdjPAD;
+    const int X0 = ox + 1 + L::TX * blockIdx.x - kAdjPAD;
     const int Y0 = TY * blockIdx.y + g.halo - 1;
 
     auto issue = [&](int p) {
@@ -242,19 +284,37 @@ __global__ void __launch_bounds__(32 * TY, 2)
     const float* tzd2 = cf.tz + 3 * nzp2;
     const float tcx = cf.tcx, tcy = cf.tcy;
     const int r = ty + 1;
-    const int c0 = kAdjPAD + 4 * lane;
-    // tile-edge neighbour column: lane 0 needs x = -1, lane 31 x = 128; the
+    const int c0 = kAdjPAD + NA * lane;
+    // tile-edge neighbour column: lane 0 needs x = -1, lane 31 x = TX; the
     // other lanes read lane 31's address (a broadcast)
-    const int ce = (lane == 0) ? kAdjPAD - 1 : kAdjPAD + kAdjTX;
+    const int ce = (lane == 0) ? kAdjPAD - 1 : kAdjPAD + L::TX;
     const int J = TY * blockIdx.y + 1 + ty;
-    const int I0 = 1 + kAdjTX * blockIdx.x + 4 * lane;
+    const int I0 = 1 + L::TX * blockIdx.x + NA * lane;
     const bool valid = (J <= g.ny) && (I0 <= g.nx);
     const unsigned FULL = 0xffffffffu;
     int waited = 0;
     bool aborted = false;
+    // the level's vertical coefficients, loaded one level ahead so that their
+    // latency hides behind the previous level's gather (indices K-1 and K+1
+    // lie in 0..nz+1 for every level K; where a term does not exist its
+    // coefficient is selected away)
+    float q_c1p, q_c2m, q_c2, q_d1p, q_d1, q_d2, q_d2m;
+    auto fetch = [&](int K) {
+        q_c1p = __ldg(tzc1 + K + 1);
+        q_c2m = __ldg(tzc2 + K - 1);
+        q_c2 = __ldg(tzc2 + K);
+        q_d1p = __ldg(tzd1 + K + 1);
+        q_d1 = __ldg(tzd1 + K);
+        q_d2 = __ldg(tzd2 + K);
+        q_d2m = __ldg(tzd2 + K - 1);
+    };
+    if (PW_ADJ_PREFETCH) fetch(kb);
 
     for (int K = kb; K <= ke; ++K) {
         const int lp = K - pb;
+        if (!PW_ADJ_PREFETCH) fetch(K);
+        const float c1p = q_c1p, c2m = q_c2m, c2 = q_c2, d1p = q_d1p, d1 = q_d1, d2 = q_d2, d2m = q_d2m;
+        if (PW_ADJ_PREFETCH && K < ke) fetch(K + 1);
         bool ok = true;
         const int need_hi = (K + 1 <= pe) ? lp + 1 : lp;
         for (int p = (K == kb ? 0 : need_hi); p <= need_hi && ok; ++p)
@@ -266,34 +326,40 @@ __global__ void __launch_bounds__(32 * TY, 2)
             const float* Pm = stages + ((lp - 1 + S) % S) * L::STAGE;   // level K-1 (valid when K-1 >= pb)
             const float* P0 = stages + (lp % S) * L::STAGE;             // level K
             const float* Pp = stages + ((lp + 1) % S) * L::STAGE;       // level K+1 (valid when K+1 <= pe)
-            // X[0..5] = the row at x = -1..4 relative to the thread's first cell
-            auto row = [&](const float* P, int f, int dj, float (&X)[6], bool lo, bool hi) {
-                const float* q = P + f * L::FIELD + (r + dj) * kAdjBW;
-                const float4 t = *reinterpret_cast<const float4*>(q + c0);
-                X[1] = t.x;
-                X[2] = t.y;
-                X[3] = t.z;
-                X[4] = t.w;
-                X[0] = X[5] = 0.f;
+            // X[0..NA+1] = the row at x = -1..NA relative to the thread's first cell
+            auto row = [&](const float* P, int f, int dj, float (&X)[NA + 2], bool lo, bool hi) {
+                const float* q = P + f * L::FIELD + (r + dj) * L::BW;
+                if constexpr (NA == 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(q + c0);
+                    X[1] = t.x;
+                    X[2] = t.y;
+                    X[3] = t.z;
+                    X[4] = t.w;
+                } else {
+                    const float2 t = *reinterpret_cast<const float2*>(q + c0);
+                    X[1] = t.x;
+                    X[2] = t.y;
+                }
+                X[0] = X[NA + 1] = 0.f;
                 if (lo || hi) {
                     const float e = q[ce];
                     if (lo) {
-                        const float m = __shfl_up_sync(FULL, t.w, 1);
+                        const float m = __shfl_up_sync(FULL, X[NA], 1);
                         X[0] = lane == 0 ? e : m;
                     }
                     if (hi) {
-                        const float pv = __shfl_down_sync(FULL, t.x, 1);
-                        X[5] = lane == 31 ? e : pv;
+                        const float pv = __shfl_down_sync(FULL, X[1], 1);
+                        X[NA + 1] = lane == 31 ? e : pv;
                     }
                 }
             };
             // rows: [L]ambda or field, level (0: K, p: K+1, m: K-1), row (m, z, p: j-1, j, j+1)
-            float LU0m[6], LU0z[6], LU0p[6], LUpz[6], LUmz[6];
-            float LV0m[6], LV0z[6], LV0p[6], LVpz[6], LVpm[6], LVmz[6];
-            float LW0m[6], LW0z[6], LW0p[6], LWmz[6], LWmp[6], LWpz[6];
-            float U0z[6], U0p[6], Upz[6];
-            float V0m[6], V0z[6], V0p[6], Vpz[6], Vpm[6];
-            float W0z[6], W0p[6], Wmz[6], Wmp[6], Wpz[6];
+            float LU0m[NA + 2], LU0z[NA + 2], LU0p[NA + 2], LUpz[NA + 2], LUmz[NA + 2];
+            float LV0m[NA + 2], LV0z[NA + 2], LV0p[NA + 2], LVpz[NA + 2], LVpm[NA + 2], LVmz[NA + 2];
+            float LW0m[NA + 2], LW0z[NA + 2], LW0p[NA + 2], LWmz[NA + 2], LWmp[NA + 2], LWpz[NA + 2];
+            float U0z[NA + 2], U0p[NA + 2], Upz[NA + 2];
+            float V0m[NA + 2], V0z[NA + 2], V0p[NA + 2], Vpz[NA + 2], Vpm[NA + 2];
+            float W0z[NA + 2], W0p[NA + 2], Wmz[NA + 2], Wmp[NA + 2], Wpz[NA + 2];
             row(P0, 3, -1, LU0m, false, false);
             row(P0, 3, 0, LU0z, true, true);
             row(P0, 3, 1, LU0p, true, false);
@@ -326,10 +392,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
             row(Pp, 2, 0, Wpz, false, false);
 
             const bool has_m = (K - 1 >= 1), has_p = (K + 1 <= nz);
-            const float c1p = has_p ? tzc1[K + 1] : 0.f, c2m = has_m ? tzc2[K - 1] : 0.f, c2 = tzc2[K];
-            const float d1p = has_p ? tzd1[K + 1] : 0.f, d1 = tzd1[K], d2 = tzd2[K];
-            const float d2m = has_m ? tzd2[K - 1] : 0.f;
-            float ru[4], rv[4], rw[4];
+            float ru[NA], rv[NA], rw[NA];
 
             // the gather of one level; EDGE: levels where some terms do not exist
             auto body = [&](auto edge_tag) {
@@ -343,7 +406,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
                 auto keep = [](bool c, float t) { return EDGE ? (c ? t : 0.f) : t; };
                 if (EDGE) {   // sensitivities of level K outside the scheme's outputs are ignored
 #pragma unroll
-                    for (int x = 0; x < 6; ++x) {
+                    for (int x = 0; x < NA + 2; ++x) {
                         LU0m[x] = keep(lu0, LU0m[x]);
                         LU0z[x] = keep(lu0, LU0z[x]);
                         LU0p[x] = keep(lu0, LU0p[x]);
@@ -356,7 +419,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < NA; ++c) {
                     const int o = c + 1;   // the cell in the X arrays; o-1 and o+1 its x neighbours
                     float a = 0.f, b = 0.f;
                     // ---- gu
@@ -426,23 +489,29 @@ __global__ void __launch_bounds__(32 * TY, 2)
 
             if (valid) {
                 const long long o = g.origin + (long long)K * g.pk + (long long)J * g.pj + I0;
-                float4 bu = make_float4(0.f, 0.f, 0.f, 0.f), bv = bu, bw = bu;
+                float bu[NA], bv[NA], bw[NA];
                 if (accumulate) {
-                    bu = *reinterpret_cast<const float4*>(gu + o);
-                    bv = *reinterpret_cast<const float4*>(gv + o);
-                    bw = *reinterpret_cast<const float4*>(gw + o);
+                    adj_ldv<NA>(gu + o, bu);
+                    adj_ldv<NA>(gv + o, bv);
+                    adj_ldv<NA>(gw + o, bw);
                 } else if (add_lambda) {   // the raw sensitivities of level K
-                    const float* q = P0 + (r)*kAdjBW + c0;
-                    bu = *reinterpret_cast<const float4*>(q + 3 * L::FIELD);
-                    bv = *reinterpret_cast<const float4*>(q + 4 * L::FIELD);
-                    bw = *reinterpret_cast<const float4*>(q + 5 * L::FIELD);
+                    const float* q = P0 + r * L::BW + c0;
+                    adj_ldv<NA>(q + 3 * L::FIELD, bu);
+                    adj_ldv<NA>(q + 4 * L::FIELD, bv);
+                    adj_ldv<NA>(q + 5 * L::FIELD, bw);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) bu[c] = bv[c] = bw[c] = 0.f;
                 }
-                *reinterpret_cast<float4*>(gu + o) = make_float4(fmaf(alpha, ru[0], bu.x), fmaf(alpha, ru[1], bu.y),
-                                                                 fmaf(alpha, ru[2], bu.z), fmaf(alpha, ru[3], bu.w));
-                *reinterpret_cast<float4*>(gv + o) = make_float4(fmaf(alpha, rv[0], bv.x), fmaf(alpha, rv[1], bv.y),
-                                                                 fmaf(alpha, rv[2], bv.z), fmaf(alpha, rv[3], bv.w));
-                *reinterpret_cast<float4*>(gw + o) = make_float4(fmaf(alpha, rw[0], bw.x), fmaf(alpha, rw[1], bw.y),
-                                                                 fmaf(alpha, rw[2], bw.z), fmaf(alpha, rw[3], bw.w));
+#pragma unroll
+                for (int c = 0; c < NA; ++c) {
+                    bu[c] = fmaf(alpha, ru[c], bu[c]);
+                    bv[c] = fmaf(alpha, rv[c], bv[c]);
+                    bw[c] = fmaf(alpha, rw[c], bw[c]);
+                }
+                adj_stv<NA>(gu + o, bu);
+                adj_stv<NA>(gv + o, bv);
+                adj_stv<NA>(gw + o, bw);
             }
         }
         __syncthreads();
@@ -464,33 +533,79 @@ __global__ void __launch_bounds__(32 * TY, 2)
     }
 }
 
-// Rows per CTA and ring slots (levels k-1, k, k+1 resident, the rest in
-// flight).  Measured on GB300 (512^2 x 64): 4 rows / 5 slots 78.7, 4 / 4 79.5,
-// 5 / 4 83.1, 6 / 4 81.8 Gcell/s; 5 rows and 4 slots fit two CTAs of 160
-// threads (91 KB of shared memory, 165 registers) on an SM: 10 warps.
+// Instantiated launch shapes (cells per thread, rows per CTA, ring slots;
+// levels k-1, k, k+1 resident, the rest in flight).  Measured on GB300 with
+// the automatic k segments, Gcell/s at 512^2 / 1024^2 / 2048^2 x 64:
+//   4 cells: 4 rows 85.4 / 99.3 / 105.3, 5 rows 82.4 / 97.8 / 103.3,
+//            6 rows 93.9 / 113.8 / 121.3 (two CTAs of 6 warps per SM);
+//   2 cells: 4 rows 90.1 / 105.9 / 111.7, 5 rows 90.2 / 103.4 / 110.1,
+//            6 rows 84.5 / 98.7 / 104.0, 8 rows 82.4 / 95.1 / 102.5;
+// 3 slots (no plane in flight beyond k+1) lose a third.  Two cells a
+// thread halve the registers (96 against 165-182) and double the warps per
+// SM, but that gains little: the gather is not bound by latency alone.
+#define PW_ADJ_CONFIGS(X) X(4, 5, 4) X(4, 4, 4) X(4, 6, 4) X(2, 4, 4) X(2, 5, 4) X(2, 6, 4) X(2, 8, 4) X(2, 8, 3)
+
+// The automatic shape (the fastest measured).
+#ifndef PW_ADJ_NA
+#define PW_ADJ_NA 4
+#endif
 #ifndef PW_ADJ_TY
-#define PW_ADJ_TY 5
+#define PW_ADJ_TY 6
 #endif
 #ifndef PW_ADJ_S
 #define PW_ADJ_S 4
 #endif
-constexpr int kAdjTY = PW_ADJ_TY, kAdjS = PW_ADJ_S;
 
-cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
-                               float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
-                               cudaStream_t s) {
-    using L = AdjLayout<kAdjTY, kAdjS>;
-    auto kern = adjoint_vec_kernel<kAdjTY, kAdjS>;
+AdjConfig adjoint_default_config() { return AdjConfig{PW_ADJ_NA, PW_ADJ_TY, PW_ADJ_S, 0}; }
+
+bool adjoint_config_supported(const AdjConfig& c) {
+#define PW_AS(NA_, TY_, S_) \
+    if (c.na == NA_ && c.ty == TY_ && c.stages == S_) return true;
+    PW_ADJ_CONFIGS(PW_AS)
+#undef PW_AS
+    return false;
+}
+
+int adjoint_blocks_per_sm(const AdjConfig& c) {
+    int n = 0;
+#define PW_AO(NA_, TY_, S_)                                                                                 \
+    if (c.na == NA_ && c.ty == TY_ && c.stages == S_) {                                                    \
+        auto kern = adjoint_vec_kernel<NA_, TY_, S_>;                                                      \
+        using L = AdjLayout<NA_, TY_, S_>;                                                                 \
+        if (set_smem_attr_once(kern, (int)L::SMEM) != cudaSuccess) return 0;                               \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * TY_, L::SMEM) != cudaSuccess) return 0; \
+        return n;                                                                                          \
+    }
+    PW_ADJ_CONFIGS(PW_AO)
+#undef PW_AO
+    return 0;
+}
+
+template <int NA, int TY, int S>
+static cudaError_t launch_adj_inst(const GridDev& g, int ox, const AdjMaps& m, float* gu, float* gv, float* gw,
+                                   float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
+                                   cudaStream_t s) {
+    using L = AdjLayout<NA, TY, S>;
+    auto kern = adjoint_vec_kernel<NA, TY, S>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
-    AdjMaps m;
-    for (int f = 0; f < 6; ++f) m.m[f] = maps6[f];
-    dim3 grid((g.nx + kAdjTX - 1) / kAdjTX, (g.ny + kAdjTY - 1) / kAdjTY, nseg);
-    kern<<<grid, dim3(32, kAdjTY), L::SMEM, s>>>(m, gu, gv, gw, g, ox, nseg, cf, alpha, accumulate, add_lambda, err);
+    dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
+    kern<<<grid, dim3(32, TY), L::SMEM, s>>>(m, gu, gv, gw, g, ox, nseg, cf, alpha, accumulate, add_lambda, err);
     return cudaGetLastError();
 }
 
-int adjoint_tma_rows() { return kAdjTY; }
+cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
+                               float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
+                               const AdjConfig& c, cudaStream_t s) {
+    AdjMaps m;
+    for (int f = 0; f < 6; ++f) m.m[f] = maps6[f];
+#define PW_AD(NA_, TY_, S_)                                                                                   \
+    if (c.na == NA_ && c.ty == TY_ && c.stages == S_)                                                         \
+        return launch_adj_inst<NA_, TY_, S_>(g, ox, m, gu, gv, gw, alpha, accumulate, add_lambda, cf, nseg, err, s);
+    PW_ADJ_CONFIGS(PW_AD)
+#undef PW_AD
+    return cudaErrorInvalidConfiguration;
+}
 
 cudaError_t launch_adjoint(const GridDev& g, const float* u, const float* v, const float* w, const float* lu,
                            const float* lv, const float* lw, float* gu, float* gv, float* gw, float alpha,

@@ -82,6 +82,7 @@ struct pw_handle_s {
     int steps_per_pass = 0;           // pw_step temporal blocking: 0 auto (= 1), 1, 2
     Step2Config step2_user{0, 0, 0, 0};
     Step2Config step2_auto{0, 0, 0, 0};   // ty == 0: not chosen yet
+    AdjConfig adj_user{0, 0, 0, 0};       // TMA adjoint shape; 0 = automatic
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
     // pw_tendencies_host staging and its copy / compute pipeline
@@ -459,6 +460,62 @@ static Step2Config choose_step2(pw_handle_t h) {
     return c;
 }
 
+// Launch shape of the TMA adjoint: each field the user fixed, else the
+// automatic shape's.  k segments (automatic): the count that minimises the
+// waves of CTAs times the planes each CTA marches (its levels plus the two
+// it reads beyond them); segments keep >= 8 levels.  The adjoint holds few
+// CTAs per SM (2 to 5), so a partly filled last wave costs much: at
+// 512^2 x 64 with 64 x 4 tiles, 1024 CTAs fill 760 slots 1.35 times, and two
+// segments turn that into 2.7 waves of half-length CTAs.
+static AdjConfig choose_adjoint(pw_handle_t h) {
+    const AdjConfig d = adjoint_default_config();
+    const AdjConfig& u = h->adj_user;
+    AdjConfig c{u.na ? u.na : d.na, u.ty ? u.ty : d.ty, u.stages ? u.stages : d.stages, u.nseg};
+    const pw_grid_t& gr = h->grid;
+    if (!c.nseg) {
+        const int tx = 32 * c.na;
+        const long long tiles = (long long)((gr.nx + tx - 1) / tx) * ((gr.ny + c.ty - 1) / c.ty);
+        int bps = adjoint_blocks_per_sm(c);
+        if (bps < 1) bps = 1;
+        const long long slots = (long long)h->num_sms * bps;
+        c.nseg = 1;
+        double best = 0.0;
+        for (int n = 1; n <= 16 && (n == 1 || gr.nz / n >= 8); ++n) {
+            const long long waves = (tiles * n + slots - 1) / slots;
+            const double cost = (double)waves * ((double)gr.nz / n + 2.0);
+            if (n == 1 || cost < 0.999 * best) {
+                best = cost;
+                c.nseg = n;
+            }
+        }
+    }
+    if (c.nseg > gr.nz) c.nseg = gr.nz;
+    return c;
+}
+
+pw_status_t pw_set_adjoint_config(pw_handle_t h, int32_t cells, int32_t ty, int32_t stages, int32_t nseg) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    if (cells < 0 || ty < 0 || stages < 0) return fail(PW_ERR_ARG, "cells, ty and stages must be >= 0");
+    if (nseg < 0 || nseg > h->grid.nz) return fail(PW_ERR_ARG, "nseg must be in 0..nz");
+    const AdjConfig d = adjoint_default_config();
+    const AdjConfig c{cells ? cells : d.na, ty ? ty : d.ty, stages ? stages : d.stages, nseg};
+    if (!adjoint_config_supported(c))
+        return fail(PW_ERR_UNSUPPORTED, "no TMA adjoint instance for cells=%d ty=%d stages=%d", c.na, c.ty,
+                    c.stages);
+    h->adj_user = AdjConfig{cells, ty, stages, nseg};
+    return PW_OK;
+}
+
+pw_status_t pw_get_adjoint_config(pw_handle_t h, int32_t out[4]) {
+    if (!h || !out) return fail(PW_ERR_ARG, "handle or out is NULL");
+    const AdjConfig c = choose_adjoint(h);
+    out[0] = c.na;
+    out[1] = c.ty;
+    out[2] = c.stages;
+    out[3] = c.nseg;
+    return PW_OK;
+}
+
 pw_status_t pw_get_tma_config(pw_handle_t h, int32_t step, int32_t out[6]) {
     if (!h || !out) return fail(PW_ERR_ARG, "handle or out is NULL");
     const TmaConfig c = choose_tma(h, step != 0);
@@ -637,6 +694,88 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
     return PW_OK;
 }
 
+// Storage scales of a step call: the state is read and written with the same
+// per-field scale (NULL = 1).
+static pw_status_t step_scales(const float* scale, Scales* sc, bool* scaled) {
+    *scaled = false;
+    for (int q = 0; q < 3; ++q) {
+        const float x = scale ? scale[q] : 1.f;
+        if (!(x > 0.f) || !(x < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
+        sc->in[q] = x;
+        sc->out[q] = 1.f / x;   // the next state is stored with the same scale
+        if (x != 1.f) *scaled = true;
+    }
+    return PW_OK;
+}
+
+// One single-step pass src -> dst (interior levels 1..nz and the periodic
+// images of the lateral halo), on the TMA k-march or the generic kernel.
+static pw_status_t step_pass(pw_handle_t h, const GridDev& g, const void* const* src, void* const* dst,
+                             const Scales& sc, bool scaled, const CoefDev& cf, float dt, bool use_tma, int ox,
+                             const TmaConfig& c, cudaStream_t s) {
+    const pw_dtype_t dtp = h->grid.dtype;
+    cudaError_t e;
+    if (use_tma) {
+        CUtensorMap maps[3];
+        for (int q = 0; q < 3; ++q) {
+            pw_status_t st = encode_map(h, src[q], c.lx, c.ty, &maps[q], c.nc);
+            if (st != PW_OK) return st;
+        }
+        e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c, s);
+        // the single-step k-march writes the images of a one-cell halo only
+        for (int q = 0; q < 3 && e == cudaSuccess && g.halo != 1; ++q)
+            e = launch_fill_halo(dtp, g, dst[q], h->num_sms, s);
+    } else {
+        e = launch_step_generic(dtp, g, src[0], src[1], src[2], dst[0], dst[1], dst[2], sc, scaled, cf, dt,
+                                h->num_sms, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    return PW_OK;
+}
+
+// TMA or generic for the step entry points: what pw_set_kernel asked for,
+// else TMA when the layout and every pointer qualify.
+static pw_status_t step_kernel_choice(pw_handle_t h, void* const* bufs, int n, bool* use_tma, int* ox) {
+    const char* why = "";
+    const bool layout_ok = tma_layout_ok(h->grid, ox, &why);
+    bool ptrs_ok = true;
+    for (int a = 0; a < n; ++a) ptrs_ok = ptrs_ok && aligned16(bufs[a]);
+    if (h->kernel_kind == 2) {
+        if (!layout_ok) return fail(PW_ERR_UNSUPPORTED, "TMA kernel requested but %s", why);
+        if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
+    }
+    *use_tma = (h->kernel_kind == 2) || (h->kernel_kind == 0 && layout_ok && ptrs_ok);
+    return PW_OK;
+}
+
+pw_status_t pw_step_to(pw_handle_t h, const void* u, const void* v, const void* w, void* nu, void* nv, void* nw,
+                       float dt, const float* scale, pw_stream_t stream) {
+    if (!h) return fail(PW_ERR_ARG, "handle is NULL");
+    void* bufs[6] = {const_cast<void*>(u), const_cast<void*>(v), const_cast<void*>(w), nu, nv, nw};
+    for (int a = 0; a < 6; ++a) {
+        if (!bufs[a]) return fail(PW_ERR_ARG, "a field pointer is NULL");
+        for (int b = 0; b < a; ++b)
+            if (bufs[a] == bufs[b]) return fail(PW_ERR_ARG, "the six fields must be distinct buffers");
+    }
+    if (!(dt == dt) || dt > 3.0e38f || dt < -3.0e38f) return fail(PW_ERR_ARG, "dt must be finite");
+    Scales sc;
+    bool scaled = false;
+    pw_status_t st = step_scales(scale, &sc, &scaled);
+    if (st != PW_OK) return st;
+    bool use_tma = false;
+    int ox = 0;
+    st = step_kernel_choice(h, bufs, 6, &use_tma, &ox);
+    if (st != PW_OK) return st;
+    const GridDev g = to_dev(h->grid);
+    CoefDev cf{h->tcx, h->tcy, h->d_tz};
+    TmaConfig c{};
+    if (use_tma) c = choose_tma(h, true);
+    st = step_pass(h, g, bufs, bufs + 3, sc, scaled, cf, dt, use_tma, ox, c, reinterpret_cast<cudaStream_t>(stream));
+    if (st != PW_OK) return st;
+    h->last_kernel = use_tma ? 2 : 1;
+    return PW_OK;
+}
+
 pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void* tmp_v, void* tmp_w, float dt,
                     int32_t nsteps, const float* scale, pw_stream_t stream) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
@@ -650,13 +789,8 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     if (!(dt == dt) || dt > 3.0e38f || dt < -3.0e38f) return fail(PW_ERR_ARG, "dt must be finite");
     Scales sc;
     bool scaled = false;
-    for (int q = 0; q < 3; ++q) {
-        const float x = scale ? scale[q] : 1.f;
-        if (!(x > 0.f) || !(x < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
-        sc.in[q] = x;
-        sc.out[q] = 1.f / x;   // the next state is stored with the same scale
-        if (x != 1.f) scaled = true;
-    }
+    pw_status_t sst = step_scales(scale, &sc, &scaled);
+    if (sst != PW_OK) return sst;
     const GridDev g = to_dev(h->grid);
     CoefDev cf{h->tcx, h->tcy, h->d_tz};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -666,15 +800,9 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
         if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
     }
     int ox = 0;
-    const char* why = "";
-    const bool layout_ok = tma_layout_ok(h->grid, &ox, &why);
-    bool ptrs_ok = true;
-    for (auto p : bufs) ptrs_ok = ptrs_ok && aligned16(p);
-    if (h->kernel_kind == 2) {
-        if (!layout_ok) return fail(PW_ERR_UNSUPPORTED, "TMA kernel requested but %s", why);
-        if (!ptrs_ok) return fail(PW_ERR_ALIGN, "TMA kernel requested but a field pointer is not 16-byte aligned");
-    }
-    const bool use_tma = (h->kernel_kind == 2) || (h->kernel_kind == 0 && layout_ok && ptrs_ok);
+    bool use_tma = false;
+    sst = step_kernel_choice(h, bufs, 6, &use_tma, &ox);
+    if (sst != PW_OK) return sst;
     // two steps per pass: TMA path, a lateral halo >= 2, and interior rows
     // starting at least 7 elements into their padded row (the q0 box begins
     // 7 columns before the first interior column)
@@ -693,33 +821,21 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     while (done < nsteps) {
         void** src = (passes % 2 == 0) ? bufs : bufs + 3;
         void** dst = (passes % 2 == 0) ? bufs + 3 : bufs;
-        cudaError_t e;
         if (use_tb2 && nsteps - done >= 2) {
             CUtensorMap maps[3];
             for (int q = 0; q < 3; ++q) {
                 pw_status_t st = encode_map_box(h, src[q], step2_box_width(), c2.ty + 2, &maps[q]);
                 if (st != PW_OK) return st;
             }
-            e = launch_step2_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c2, s);
+            cudaError_t e = launch_step2_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c2, s);
             done += 2;
             kind = 3;
-        } else if (use_tma) {
-            CUtensorMap maps[3];
-            for (int q = 0; q < 3; ++q) {
-                pw_status_t st = encode_map(h, src[q], c.lx, c.ty, &maps[q], c.nc);
-                if (st != PW_OK) return st;
-            }
-            e = launch_step_tma(dtp, g, ox, maps, dst[0], dst[1], dst[2], sc, cf, dt, h->d_err, c, s);
-            done += 1;
-            // the single-step k-march writes the images of a one-cell halo only
-            for (int q = 0; q < 3 && e == cudaSuccess && g.halo != 1; ++q)
-                e = launch_fill_halo(dtp, g, dst[q], h->num_sms, s);
+            if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         } else {
-            e = launch_step_generic(dtp, g, src[0], src[1], src[2], dst[0], dst[1], dst[2], sc, scaled, cf, dt,
-                                    h->num_sms, s);
+            pw_status_t st = step_pass(h, g, src, dst, sc, scaled, cf, dt, use_tma, ox, c, s);
+            if (st != PW_OK) return st;
             done += 1;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         ++passes;
     }
     h->last_kernel = kind;
@@ -767,17 +883,15 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
             if (e != cudaSuccess) return cuda_fail(e, "sensitivity halo fill");
         }
         CUtensorMap maps[6];
-        const int rows = adjoint_tma_rows();
+        const AdjConfig ac = choose_adjoint(h);
         for (int q = 0; q < 6; ++q) {
-            pw_status_t st = encode_map(h, ins[q], 32, rows, &maps[q]);
+            pw_status_t st = encode_map(h, ins[q], 32, ac.ty, &maps[q], ac.na);
             if (st != PW_OK) return st;
         }
-        const long long tiles = (long long)((g.nx + 127) / 128) * ((g.ny + rows - 1) / rows);
-        int nseg = 1;
-        while (tiles * nseg < 4LL * h->num_sms && g.nz / (nseg * 2) >= 8) nseg *= 2;
+        const int nseg = ac.nseg;
         cudaError_t e = launch_adjoint_tma(g, ox, maps, (float*)gu, (float*)gv, (float*)gw, alpha,
                                            (flags & PW_ADJ_ACCUMULATE) ? 1 : 0, (flags & PW_ADJ_ADD_LAMBDA) ? 1 : 0,
-                                           cf, nseg, h->d_err, s);
+                                           cf, nseg, h->d_err, ac, s);
         if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
         h->last_kernel = 2;
         return PW_OK;

@@ -118,12 +118,19 @@ cudaError_t launch_adjoint(const GridDev& g, const float* u, const float* v, con
                            int accumulate, int add_lambda, int periodic, const CoefDev& cf, int num_sms,
                            cudaStream_t s);
 
+// Launch shape of the TMA adjoint: na cells per thread along x (a CTA covers
+// 32*na columns), ty rows per CTA, stages ring slots.
+struct AdjConfig {
+    int na = 0, ty = 0, stages = 0, nseg = 0;
+};
 // TMA k-march adjoint (periodic mode, FP32): maps6 = u, v, w, lsu, lsv, lsw
-// encoded for 32 lanes and adjoint_tma_rows() rows; halos must be periodic.
+// encoded for 32 lanes of c.na cells and c.ty rows; halos must be periodic.
 cudaError_t launch_adjoint_tma(const GridDev& g, int ox, const CUtensorMap* maps6, float* gu, float* gv, float* gw,
                                float alpha, int accumulate, int add_lambda, const CoefDev& cf, int nseg, int* err,
-                               cudaStream_t s);
-int adjoint_tma_rows();
+                               const AdjConfig& c, cudaStream_t s);
+bool adjoint_config_supported(const AdjConfig& c);
+AdjConfig adjoint_default_config();
+int adjoint_blocks_per_sm(const AdjConfig& c);
 
 // Blocks of the TMA kernel resident per SM for a config (0 if it cannot launch).
 int tma_blocks_per_sm(pw_dtype_t dt, const TmaConfig& c);

@@ -55,11 +55,14 @@ SIGNATURES = [
     ("pw_set_tma_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
     ("pw_set_step_blocking", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     ("pw_get_tma_config", ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I32)]),
+    ("pw_set_adjoint_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    ("pw_get_adjoint_config", ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
     ("pw_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _VP]),
     ("pw_step", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _FP, _VP]),
+    ("pw_step_to", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _FP, _VP]),
     ("pw_error_norms", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32, _dp, _VP]),
     ("pw_weighted_dot_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, ctypes.c_float, _dp, _I32, _I32,
@@ -247,6 +250,18 @@ class PW:
         _check(lib().pw_get_tma_config(self.h, 1 if step else 0, out), "pw_get_tma_config")
         return dict(zip(("lanes_x", "cells", "ty", "stages", "nseg", "rows"), list(out)))
 
+    def set_adjoint_config(self, cells=0, ty=0, stages=0, nseg=0):
+        """Launch shape of the TMA adjoint (0 = automatic): cells per thread
+        along x, rows per CTA, ring slots, CTAs along z."""
+        _check(lib().pw_set_adjoint_config(self.h, int(cells), int(ty), int(stages), int(nseg)),
+               "pw_set_adjoint_config")
+
+    def adjoint_config(self):
+        """The TMA adjoint's launch shape: dict(cells, ty, stages, nseg)."""
+        out = (_I32 * 4)()
+        _check(lib().pw_get_adjoint_config(self.h, out), "pw_get_adjoint_config")
+        return dict(zip(("cells", "ty", "stages", "nseg"), list(out)))
+
     def set_step_blocking(self, steps_per_pass=0, ty=0, stages=0, ctas_per_sm=0, nseg=0):
         """Temporal blocking of step(): 1 or 2 steps per kernel pass (0 =
         automatic = 1; 2 needs the TMA path and a halo >= 2), and the
@@ -286,6 +301,18 @@ class PW:
         _check(lib().pw_step(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"), _ptr(tmp_u, g, "tmp_u"),
                              _ptr(tmp_v, g, "tmp_v"), _ptr(tmp_w, g, "tmp_w"), float(dt), int(nsteps),
                              sp[0] if sp else None, _stream_ptr(stream)), "pw_step")
+
+    def step_to(self, u, v, w, nu, nv, nw, dt, scale=None, stream=None):
+        """One forward-Euler step out of place: (nu, nv, nw) = q + dt*s(q) with
+        the result's periodic halo; the halos of (u, v, w) must be periodic."""
+        g = self.grid
+        sp = None
+        if scale is not None:
+            arr = (ctypes.c_float * 3)(*[float(x) for x in scale])
+            sp = (ctypes.cast(arr, _FP), arr)
+        _check(lib().pw_step_to(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"), _ptr(nu, g, "nu"),
+                                _ptr(nv, g, "nv"), _ptr(nw, g, "nw"), float(dt), sp[0] if sp else None,
+                                _stream_ptr(stream)), "pw_step_to")
 
     def adjoint(self, u, v, w, lsu, lsv, lsw, gu, gv, gw, alpha=1.0, flags=0, stream=None):
         """g = [g | l | 0] + alpha * J(u,v,w)^T l (see pw_adjoint for flags)."""

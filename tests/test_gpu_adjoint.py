@@ -1,7 +1,8 @@
 """pw_adjoint and the autograd rollout through the C ABI, against the oracle.
 
   * full-array adjoint vs oracle.adjoint_tendencies on every cell it writes;
-  * periodic adjoint vs the oracle's adjoint folded onto the interior;
+  * periodic adjoint vs the oracle's adjoint folded onto the interior, for
+    the generic kernel and every instantiated TMA launch shape;
   * ACCUMULATE and ADD_LAMBDA modes;
   * the rollout gradient (PWRollout, checkpointed) vs oracle.step_adjoint and
     vs central finite differences of the GPU rollout.
@@ -86,6 +87,50 @@ def test_adjoint_periodic_matches_folded_oracle(shape, kernel):
         assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
         v = g.view(o)
         assert torch.isnan(v[1:-1, 0]).all() and torch.isnan(v[1:-1, :, 0]).all()   # halo not written
+
+
+ADJ_SHAPES = [(4, 5, 4), (4, 4, 4), (4, 6, 4), (2, 4, 4), (2, 5, 4), (2, 6, 4), (2, 8, 4), (2, 8, 3)]
+
+
+@pytest.mark.parametrize("cfg", ADJ_SHAPES, ids=[f"c{a}_ty{b}_s{c}" for a, b, c in ADJ_SHAPES])
+def test_adjoint_tma_shapes_match_folded_oracle(cfg):
+    """Every instantiated TMA adjoint shape on a grid ragged in x (260 = 2 x 128
+    + 4 = 4 x 64 + 4), in y (19 rows) and in z (4 k segments of 10 levels)."""
+    c, q, lam, g, h, dq, dl = _setup(260, 19, 40, periodic_q=True)
+    h.set_adjoint_config(*cfg, nseg=4)
+    assert h.adjoint_config() == dict(zip(("cells", "ty", "stages", "nseg"), cfg + (4,)))
+    out = [g.alloc(fill=NAN) for _ in range(3)]
+    h.adjoint(*dq, *dl, *out, alpha=1.0, flags=pwlib.PW_ADJ_PERIODIC)
+    h.sync()
+    assert h.last_kernel == 2
+    lam_int = []
+    for x in lam:
+        y = np.zeros(x.shape)
+        y[1:-1, 1:-1, 1:-1] = x.numpy()[1:-1, 1:-1, 1:-1]
+        lam_int.append(y)
+    full = oracle.adjoint_tendencies(*[x.numpy() for x in q], c, *lam_int)
+    for o, r in zip(out, full):
+        ref = oracle.fold_halo_periodic(r)[1:-1, 1:-1, 1:-1]
+        got = g.to_dense(o).numpy()[1:-1, 1:-1, 1:-1]
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+        v = g.view(o)
+        assert torch.isnan(v[1:-1, 0]).all() and torch.isnan(v[1:-1, :, 0]).all()   # halo not written
+
+
+def test_adjoint_config_rejections():
+    g = pwlib.Grid(64, 8, 4)
+    h = pwlib.PW(g, inputs.make_coeffs(4))
+    auto = h.adjoint_config()
+    assert (auto["cells"], auto["ty"], auto["stages"]) in ADJ_SHAPES and auto["nseg"] == 1
+    for bad in [(3, 0, 0), (2, 7, 4), (4, 8, 4)]:
+        with pytest.raises(pwlib.PwError) as e:
+            h.set_adjoint_config(*bad)
+        assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
+    for bad in [(-1, 0, 0, 0), (0, 0, 0, 5), (0, 0, 0, -1)]:
+        with pytest.raises(pwlib.PwError) as e:
+            h.set_adjoint_config(*bad)
+        assert e.value.status == pwlib.PW_ERR_ARG
+    assert h.adjoint_config() == auto
 
 
 @pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
@@ -183,3 +228,21 @@ def test_rollout_gradient_central_differences():
 
     fd = (L_at(eps) - L_at(-eps)) / (2 * eps)
     assert abs(fd - ana) <= 2e-3 * abs(ana)
+
+
+def test_rollout_forward_equals_in_place_steps():
+    """The rollout's out-of-place steps give the bits of pw_step run in place,
+    and the returned state holds no unset entries."""
+    nx, ny, nz = 64, 24, 16
+    c, f, g, h, q0, ut = _rollout_case(nx, ny, nz, 7, 3)
+    outs = rollout(*q0, h, 1.0, 7, 3)
+    q = [t.detach().clone() for t in q0]
+    tmp = [g.alloc() for _ in range(3)]
+    h.step(*q, *tmp, 1.0, 7)
+    h.sync()
+    for a, b in zip(outs, q):
+        assert torch.equal(g.view(a)[1:-1], g.view(b)[1:-1])
+        assert torch.isfinite(a).all()
+    z = rollout(*q0, h, 1.0, 0, 3)
+    for a, b in zip(z, q0):
+        assert torch.equal(g.view(a)[1:-1, 1:-1, 1:-1], g.view(b)[1:-1, 1:-1, 1:-1].detach())

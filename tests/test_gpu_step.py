@@ -158,3 +158,53 @@ def test_step_lowp_state(dtype, bound):
         assert np.abs(interior(a) - interior(b)).max() / np.abs(interior(b)).max() <= bound
     # w starts at 0 and grows from the u, v coupling: compare against the u scale
     assert np.abs(interior(got[2]) - interior(ref[2])).max() / np.abs(interior(ref[0])).max() <= bound
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
+@pytest.mark.parametrize("dtype,halo,shape", [("f32", 1, (128, 24, 16)), ("f32", 2, (260, 13, 7)),
+                                              ("bf16", 1, (128, 24, 16)), ("f16", 1, (132, 9, 5))])
+def test_step_to_equals_one_in_place_step(kernel, dtype, halo, shape):
+    """pw_step_to leaves its inputs alone and writes exactly what one step of
+    pw_step leaves in place: interior and periodic halo, bit for bit."""
+    nx, ny, nz = shape
+    c = inputs.make_coeffs(nz)
+    f = inputs.smooth_fields(nx, ny, nz, w_zero=True)
+    g = pwlib.Grid(nx, ny, nz, dtype=dtype, halo=halo)
+    h = pwlib.PW(g, c)
+    h.set_kernel(kernel)
+    sc = None
+    if dtype == "f16":
+        sc = precision.suggest_scales([float(x.abs().max()) for x in f], c, dtype)[:3]
+    q = [g.from_dense(x, scale=s) for x, s in zip(f, sc or (1.0, 1.0, 1.0))]
+    for t in q:
+        h.fill_halo_periodic(t)
+    before = [t.clone() for t in q]
+    nxt = [g.alloc(fill=NAN) for _ in range(3)]
+    h.step_to(*q, *nxt, 0.5, scale=sc)
+    h.sync()
+    assert h.last_kernel == kernel
+    for a, b in zip(q, before):
+        assert torch.equal(a.view(torch.int16) if a.element_size() == 2 else a.view(torch.int32),
+                           b.view(torch.int16) if b.element_size() == 2 else b.view(torch.int32))
+    tmp = [g.alloc(fill=NAN) for _ in range(3)]
+    h.step(*q, *tmp, 0.5, 1, scale=sc)
+    h.sync()
+    for a, b in zip(nxt, q):
+        assert torch.equal(g.view(a)[1:-1], g.view(b)[1:-1])
+    if dtype == "f32":
+        ref = oracle.step(*[x.numpy() for x in f], c, 0.5, 1)
+        assert _relerr(_dense(g, nxt), ref) <= 1e-5
+
+
+def test_step_to_rejections():
+    nx, ny, nz = 64, 8, 5
+    c, f, g, h, q, tmp = _state(nx, ny, nz)
+    with pytest.raises(pwlib.PwError) as e:
+        h.step_to(*q, q[0], tmp[1], tmp[2], 1.0)
+    assert e.value.status == pwlib.PW_ERR_ARG
+    with pytest.raises(pwlib.PwError) as e:
+        h.step_to(*q, *tmp, float("nan"))
+    assert e.value.status == pwlib.PW_ERR_ARG
+    with pytest.raises(pwlib.PwError) as e:
+        h.step_to(*q, *tmp, 1.0, scale=(1.0, 0.0, 1.0))
+    assert e.value.status == pwlib.PW_ERR_ARG
