@@ -12,8 +12,10 @@ N > 1 (torchrun): every rank runs its own independent grid of the same size
 (independent problems, no data-path collective; weak scaling); the timed
 region is bracketed by a barrier and the max over ranks is reported.
 
---impl reference times the CPU oracle (plain C loop nest, FP64, one thread)
-on bounded slabs of the same workload, on rank 0 only.
+--impl reference times the CPU oracle (plain C loop nest, FP64, unchanged)
+on bounded slabs of the same workload, one thread per host core, on rank 0
+only.  --form selects another form of the path (16-bit storage, fused steps,
+two steps per pass, batch, adjoint rollout, small-grid latency, host link).
 """
 import argparse
 import hashlib
@@ -407,7 +409,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": workload_label(w), "nx": nx, "ny": ny, "nz": nz, "cells_per_gpu": cells,
                    "l2": "inputs larger than L2 (3 x %.2f GB resident per grid)" % (grid.alloc_elems * 4 / 1e9),
                    "kernel": "TMA k-march (pw_tendencies, automatic launch shape)",
-                   "parallelism": f"{world} independent grids, one per GPU"},
+                   "parallelism": f"{world} independent grid{'s' if world > 1 else ''}, one per GPU"},
         "hbm_frac_of_measured": achieved / peak,
         "gflops_useful": value * FLOPS_PER_CELL,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -130,8 +130,9 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
  * choice, which depends on the call: (32, 4, 4, 4, 1) for FP32;
  * (32, 8, 4, 4, 2) for the source terms with 16-bit storage; (16, 8, 4, 8, 1)
  * for fused steps with 16-bit storage when nx is a multiple of 8 (else
- * (32, 4, 4, 4, 1)); (16, 4, 4, 4, 1) when nx <= 64; nseg as many as keep
- * about two waves of CTAs, at least 2 levels each.  Instantiated (lanes_x,
+ * (32, 4, 4, 4, 1)); (16, 4, 4, 4, 1) when nx <= 64; nseg the count that
+ * best fills the last wave of CTAs per plane marched (segments of >= 2
+ * levels; more segments only for a >= 3 % gain).  Instantiated (lanes_x,
  * ty, stages, cells, rows_per_thread): (32,4,4,4,1) (32,8,3,4,1) (32,8,4,4,1)
  * (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1) (16,8,4,4,1), and for 16-bit
  * storage also (16,4,4,8,1) (16,8,4,8,1) (32,8,4,4,2) (32,16,4,4,2)

@@ -255,11 +255,26 @@ static TmaConfig choose_tma(pw_handle_t h, bool step) {
         int bps = tma_blocks_per_sm(gr.dtype, c);
         if (bps < 1) bps = 1;
         const long long slots = (long long)h->num_sms * bps;
-        // down to 2 levels per segment: a small grid is a short serial march
-        // (64^3 FP32 in a CUDA graph: 7.0 us per call with 8 segments, 4.0
-        // with 32 on 64-column tiles); large grids stop at one segment
+        // the count that minimises (waves of CTAs) x (planes each CTA marches:
+        // its levels plus the two beyond them), down to 2 levels per segment;
+        // more segments only for a gain of >= 3 %; and a single wave is
+        // widened to two when that costs <= 5 % (one partial wave leaves SMs
+        // with unequal CTA counts).  Measured on GB300 (FP32, 64 levels,
+        // Gcell/s): 256^2 145 -> 181 (4 segments instead of 16), 1024^2
+        // 236 -> 249 (2 instead of 1), 512^2 216 (1 segment) / 221 (2); 64^3
+        // keeps 32 segments of 2 levels (4.0 us per call in a CUDA graph, 7.0
+        // with 8)
+        auto waves = [&](int n) { return (tiles * n + slots - 1) / slots; };
+        auto cost = [&](int n) { return (double)waves(n) * ((double)gr.nz / n + 2.0); };
         int nseg = 1;
-        while (tiles * nseg < 2 * slots && gr.nz / (nseg * 2) >= 2) nseg *= 2;
+        for (int n = 2; gr.nz / n >= 2; ++n)
+            if (cost(n) < 0.97 * cost(nseg)) nseg = n;
+        if (waves(nseg) < 2)
+            for (int n = nseg + 1; gr.nz / n >= 2; ++n)
+                if (waves(n) >= 2) {
+                    if (cost(n) <= 1.05 * cost(nseg)) nseg = n;
+                    break;
+                }
         c.nseg = nseg;
     }
     if (c.nseg > gr.nz / 2) c.nseg = std::max(1, gr.nz / 2);
