@@ -509,12 +509,13 @@ STEP2_SHAPES = [(8, 3, 1), (8, 3, 2), (8, 4, 1), (12, 3, 1), (16, 3, 1), (16, 4,
 
 
 def form_step(args, dtype, spp=1):
-    """Fused forward-Euler steps on 2048 x 2048 x 64: one step per kernel
-    pass (spp = 1, halo-1 grid) or two (spp = 2, halo-2 grid, every
-    instantiated launch shape timed; the value is the automatic shape's)."""
+    """Fused forward-Euler steps on 2048 x 2048 x 64 (512 x 512 x 64 with
+    --workload 512, for profiling): one step per kernel pass (spp = 1, halo-1
+    grid) or two (spp = 2, halo-2 grid, every instantiated launch shape timed;
+    the value is the automatic shape's)."""
     import paper_2301_13016_gb300 as pwlib
     from paper_2301_13016_gb300 import inputs, precision
-    nx = ny = 2048
+    nx = ny = int(args.workload)
     nz = 64
     stream = torch.cuda.current_stream()
     ref = None if args.skip_fp32_ref else _fp32_reference_rate(nx, ny, nz, max(20, args.steps // 4), stream)
@@ -814,15 +815,50 @@ def form_hostlink(args):
             for q in range(3):
                 hout[q][lo:hi].copy_(dout[q][lo:hi], non_blocking=True)
 
+    # the same bytes with one copy stream per field (several copy engines)
+    s3 = [torch.cuda.Stream() for _ in range(3)]
+
+    def h2d3():
+        for q in range(3):
+            with torch.cuda.stream(s3[q]):
+                din[q][lo:hi].copy_(hin[q][lo:hi], non_blocking=True)
+
+    def d2h3():
+        for q in range(3):
+            with torch.cuda.stream(s3[q]):
+                hout[q][lo:hi].copy_(dout[q][lo:hi], non_blocking=True)
+
+    # the link without copy engines: SM loads from / stores to pinned host
+    # memory through a device view of it (unified addressing)
+    class _HostView:
+        def __init__(self, t):
+            self.__cuda_array_interface__ = {"data": (t.data_ptr(), False), "shape": (t.numel(),),
+                                             "typestr": "<f4", "version": 3}
+
+    hv_in = [torch.as_tensor(_HostView(t), device="cuda") for t in hin]
+    hv_out = [torch.as_tensor(_HostView(t), device="cuda") for t in hout]
+
+    def sm_read():
+        for q in range(3):
+            torch.add(hv_in[q][lo:hi], 0.0, out=din[q][lo:hi])
+
+    def sm_write():
+        for q in range(3):
+            torch.add(dout[q][lo:hi], 0.0, out=hv_out[q][lo:hi])
+
     reps = max(2, min(args.steps, 10))
     t_in, t_out = wall(h2d, reps), wall(d2h, reps)
     t_both = wall(lambda: (h2d(), d2h()), reps)
+    t_in3, t_out3 = wall(h2d3, reps), wall(d2h3, reps)
+    t_smr, t_smw = wall(sm_read, reps), wall(sm_write, reps)
     t_path = wall(lambda: h.tendencies_host(*hin, *hout), reps)
     val = g.cells / t_path / 1e9
     _form_line(args, "hostlink", "PW tendencies end to end through host buffers, against the host-link bound", val,
                "Gcell/s", {"workload": f"{nx}x{ny}x{nz} FP32, pinned host buffers, {gb:.2f} GB each way per call"},
                {"dtype": "f32", "ms_per_step": t_path * 1e3,
-                "copy_gbs": {"h2d_alone": gb / t_in, "d2h_alone": gb / t_out, "each_way_both_at_once": gb / t_both},
+                "copy_gbs": {"h2d_alone": gb / t_in, "d2h_alone": gb / t_out, "each_way_both_at_once": gb / t_both,
+                             "h2d_three_streams": gb / t_in3, "d2h_three_streams": gb / t_out3,
+                             "sm_loads_from_host": gb / t_smr, "sm_stores_to_host": gb / t_smw},
                 "copy_only_ms": t_both * 1e3, "bound_gcells": g.cells / t_both / 1e9,
                 "frac_of_link_bound": t_both / t_path, "h2d_bytes_per_step": int(gb * 1e9),
                 "d2h_bytes_per_step": int(gb * 1e9)})
