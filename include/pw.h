@@ -112,10 +112,12 @@ pw_status_t pw_create(const pw_grid_t *grid, const pw_coeffs_t *coeffs, pw_handl
 /* Release the handle and everything it allocated.  NULL is accepted. */
 pw_status_t pw_destroy(pw_handle_t h);
 
-/* Kernel selection for pw_tendencies: 0 = automatic (TMA k-march kernel when
- * the layout and pointers qualify, else the generic kernel), 1 = generic
- * kernel, 2 = TMA kernel (PW_ERR_UNSUPPORTED/PW_ERR_ALIGN at call time when
- * the layout or pointers do not qualify). */
+/* Kernel selection for pw_tendencies, pw_step, pw_step_to and the periodic
+ * pw_adjoint: 0 = automatic (TMA k-march kernel when the layout and pointers
+ * qualify, else the generic kernel), 1 = generic kernel, 2 = TMA kernel
+ * (pw_tendencies and the step calls return PW_ERR_UNSUPPORTED/PW_ERR_ALIGN
+ * when the layout or pointers do not qualify; pw_adjoint then runs the
+ * generic kernel). */
 pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
 
 /*
