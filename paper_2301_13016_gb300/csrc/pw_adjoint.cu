@@ -181,7 +181,8 @@ struct AdjLayout {
     static constexpr int FIELD = ((FIELD_RAW * 4 + 127) / 128) * 32;   // floats, 128-byte multiple
     static constexpr int STAGE = 6 * FIELD;
     static constexpr uint32_t TX_BYTES = 6u * FIELD_RAW * 4u;
-    static constexpr size_t SMEM = (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
+    // the ring, one mbarrier per slot, 4 flag words, one release counter per slot
+    static constexpr size_t SMEM = (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16 + 4 * S;
 };
 
 struct AdjMaps {
@@ -210,6 +211,18 @@ __device__ __forceinline__ void adj_stv(float* p, const float (&v)[NA]) {
     else
         *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
 }
+
+// How a ring slot is handed back after a level: 0 = a CTA barrier, then one
+// thread refills it; 1 = each warp counts itself out on the slot (an
+// acquire-release atomic) and the last one refills it, so warps need not
+// wait for each other at every level.  On GB300 the barrier was faster
+// (4 x 6 shape, 512^2 / 1024^2 / 2048^2 x 64: 93.5 / 113.8 / 121.1 against
+// 91.1 / 109.5 / 115.7 Gcell/s, same box), as in the forward k-march: with
+// three resident levels and four slots a warp can run at most one level
+// ahead anyway.
+#ifndef PW_ADJ_SPLIT_ARRIVE
+#define PW_ADJ_SPLIT_ARRIVE 0
+#endif
 
 // CTAs per SM a shape's register budget is sized for: what shared memory
 // allows, at most 2 for 4 cells a thread (their gather needs 165-182
@@ -243,7 +256,8 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* stages = reinterpret_cast<float*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * L::STAGE * 4);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + S);   // [0] abort, [1] planes issued
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(bars + S) + 4;              // warps done with each slot
 
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
     const int nz = g.nz, nzp2 = nz + 2;
@@ -262,14 +276,18 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
     };
     int issued = 0;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bars[s], 1);
+            cnt[s] = 0;
+        }
+        abort_flag[0] = 0;
         fence_mbar_init();
     }
     __syncthreads();
     if (tid == 0) {
         for (int f = 0; f < 6; ++f) prefetch_tensormap(&maps.m[f]);
         for (; issued < S && issued < np; ++issued) issue(issued);
+        abort_flag[1] = issued;
     }
 
     const float* tzc1 = cf.tz;
@@ -295,7 +313,7 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
         for (int p = (K == kb ? 0 : need_hi); p <= need_hi && ok; ++p)
             ok = mbar_wait_bounded(&bars[p % S], (uint32_t)((p / S) & 1), kWaitLimitNs);
         ok = __all_sync(FULL, ok);
-        if (!ok) *abort_flag = 1;
+        if (!ok) abort_flag[0] = 1;
         if (ok) {
             waited = need_hi + 1;
             const float* Pm = stages + ((lp - 1 + S) % S) * L::STAGE;   // level K-1 (valid when K-1 >= pb)
@@ -494,8 +512,29 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
                 adj_stv<NA>(gw + o, bw);
             }
         }
+#if PW_ADJ_SPLIT_ARRIVE
+        // this warp is done with plane lp-1 (level K-1); the last warp to say
+        // so refills its slot with plane lp-1+S
+        __syncwarp();
+        if (lane == 0 && ok && lp >= 1) {
+            const int s = (lp - 1) % S;
+            if (atom_add_acq_rel_cta(&cnt[s], 1u) == (uint32_t)(TY - 1)) {
+                cnt[s] = 0;
+                const int p = lp - 1 + S;
+                if (p < np) {
+                    fence_proxy_async_smem();
+                    issue(p);
+                    atomicMax(const_cast<int*>(&abort_flag[1]), p + 1);
+                }
+            }
+        }
+        if (abort_flag[0]) {
+            aborted = true;
+            break;
+        }
+#else
         __syncthreads();
-        if (*abort_flag) {
+        if (abort_flag[0]) {
             aborted = true;
             break;
         }
@@ -505,12 +544,26 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
             issue(issued);
             ++issued;
         }
+#endif
     }
+#if PW_ADJ_SPLIT_ARRIVE
+    // every warp has left the march (each wait is bounded): an abort by any
+    // warp is visible, and only the last S planes issued can be in flight
+    __syncthreads();
+    aborted = abort_flag[0] != 0;
+    if (aborted && tid == 0) {
+        report_error(err, DEV_TIMEOUT_TMA_WAIT);
+        const int hi = abort_flag[1];
+        for (int p = max(hi - S, 0); p < hi; ++p) mbar_wait_bounded(&bars[p % S], (p / S) & 1, kDrainLimitNs);
+    }
+    (void)waited;
+#else
     if (aborted && tid == 0) {
         report_error(err, DEV_TIMEOUT_TMA_WAIT);
         for (int p = waited; p < issued; ++p)
             if (!mbar_wait_bounded(&bars[p % S], (p / S) & 1, kDrainLimitNs)) break;
     }
+#endif
 }
 
 // Instantiated launch shapes (cells per thread, rows per CTA, ring slots;
