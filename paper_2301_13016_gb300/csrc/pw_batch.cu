@@ -4,7 +4,9 @@
 // The paper scales its Versal design by decomposing the problem into
 // independent compute units, each owning a 3D part of the grid (Sec. 5);
 // here the units are whole grids.  Every (grid, tile) pair is a work item;
-// the items are sorted longest first and a persistent k-march CTA per SM
+// the items go grid by grid, deepest grids first (a stable sort on nz, so
+// each grid's tiles stay together in raster order and neighbouring tiles
+// share their halo rows through L2), and a persistent k-march CTA per SM
 // slot takes the next item from an atomic counter until none is left, so
 // large and small grids share the GPU without a launch per grid.  The
 // per-grid records and TMA descriptors live in device tables that are
