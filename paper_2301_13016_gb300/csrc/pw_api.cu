@@ -83,6 +83,7 @@ struct pw_handle_s {
     Step2Config step2_user{0, 0, 0, 0};
     Step2Config step2_auto{0, 0, 0, 0};   // ty == 0: not chosen yet
     AdjConfig adj_user{0, 0, 0, 0};       // TMA adjoint shape; 0 = automatic
+    AdjConfig adj_auto{0, 0, 0, 0};       // the shape in use; na == 0: not chosen yet
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
     // pw_tendencies_host staging and its copy / compute pipeline
@@ -210,13 +211,13 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
 // (2048^2 x 64):
 //   FP32:                       32 lanes x 4 cells x 4 rows (HBM-bound);
 //   16-bit, source terms:       32 lanes x 4 cells x 8 rows, two rows per
-//                               thread in packed FP32x2 (BF16 325, FP16 299
-//                               Gcell/s; one row per thread: 305, 296);
+//                               thread in packed FP32x2 (BF16 327, FP16 332
+//                               Gcell/s with the scales folded; one row per
+//                               thread: 305, 296);
 //   16-bit, steps (nx % 8 = 0): 16 lanes x 8 cells x 8 rows (BF16 279, FP16
 //                               267 Gcell-steps/s; two rows: 266, 247);
 //   nx <= 64:                   16 lanes x 4 cells x 4 rows;
-// 4 stages, and k segments doubled while the CTAs cover fewer than about two
-// waves over the SMs, down to 2 levels per segment.
+// 4 stages, and the k segments chosen below.
 static TmaConfig choose_tma(pw_handle_t h, bool step) {
     TmaConfig& cache = h->tma_auto[step ? 1 : 0];
     if (cache.ty) return cache;
@@ -483,6 +484,7 @@ static Step2Config choose_step2(pw_handle_t h) {
 // 512^2 x 64 with 64 x 4 tiles, 1024 CTAs fill 760 slots 1.35 times, and two
 // segments turn that into 2.7 waves of half-length CTAs.
 static AdjConfig choose_adjoint(pw_handle_t h) {
+    if (h->adj_auto.na) return h->adj_auto;
     const AdjConfig d = adjoint_default_config();
     const AdjConfig& u = h->adj_user;
     AdjConfig c{u.na ? u.na : d.na, u.ty ? u.ty : d.ty, u.stages ? u.stages : d.stages, u.nseg};
@@ -505,6 +507,7 @@ static AdjConfig choose_adjoint(pw_handle_t h) {
         }
     }
     if (c.nseg > gr.nz) c.nseg = gr.nz;
+    h->adj_auto = c;
     return c;
 }
 
@@ -518,6 +521,7 @@ pw_status_t pw_set_adjoint_config(pw_handle_t h, int32_t cells, int32_t ty, int3
         return fail(PW_ERR_UNSUPPORTED, "no TMA adjoint instance for cells=%d ty=%d stages=%d", c.na, c.ty,
                     c.stages);
     h->adj_user = AdjConfig{cells, ty, stages, nseg};
+    h->adj_auto = AdjConfig{0, 0, 0, 0};
     return PW_OK;
 }
 
