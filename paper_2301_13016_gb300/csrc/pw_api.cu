@@ -381,6 +381,9 @@ pw_status_t pw_create(const pw_grid_t* grid, const pw_coeffs_t* coeffs, pw_handl
     if (e == cudaSuccess) e = cudaMemcpy(h->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    // the upload and the clear run on the legacy default stream, which the
+    // caller's non-blocking streams do not wait for: finish them here
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         pw_destroy(h);
         return cuda_fail(e, "pw_create");
@@ -609,7 +612,7 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         if (!p) {
             cudaError_t e = cudaMalloc(&p, bytes);
             if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging allocation");
-            e = cudaMemset(p, 0, bytes);
+            e = cudaMemsetAsync(p, 0, bytes, reinterpret_cast<cudaStream_t>(stream));   // before the copies
             if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging clear");
         }
     cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
@@ -994,7 +997,9 @@ pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream) {
     int flag = 0;
     PW_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status word read");
     if (flag != DEV_OK) {
-        PW_CUDA(cudaMemset(h->d_err, 0, sizeof(int)), "status word clear");
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        PW_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s), "status word clear");
+        PW_CUDA(cudaStreamSynchronize(s), "status word clear");
         return fail(PW_ERR_DEVICE_TIMEOUT, "a kernel gave up a bounded wait (code %d)", flag);
     }
     PW_CUDA(cudaGetLastError(), "pending CUDA error");

@@ -194,6 +194,9 @@ static pw_status_t build_items(pw_batch_t b) {
     cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(1, v.size()) * sizeof(int2));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_items, b->items.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    // legacy-stream upload (and, at creation, the coefficient upload and the
+    // status clear): complete before any launch on the caller's streams
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) return internal_cuda_fail(e, "batch work list upload");
     int bps = 0;
     Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
@@ -418,7 +421,8 @@ pw_status_t pw_batch_sync(pw_batch_t b, pw_stream_t stream) {
     e = cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return internal_cuda_fail(e, "status word read");
     if (flag != DEV_OK) {
-        cudaMemset(b->d_err, 0, sizeof(int));
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (cudaMemsetAsync(b->d_err, 0, sizeof(int), s) == cudaSuccess) cudaStreamSynchronize(s);
         return internal_fail(PW_ERR_DEVICE_TIMEOUT, "a batched kernel gave up a bounded wait (code %d)", flag);
     }
     return PW_OK;
