@@ -186,9 +186,13 @@ class Grid:
         return out * scale if scale != 1.0 else out
 
 
-def _ptr(t, grid, what):
+def _ptr(t, grid, what, host=False):
+    """Address of a field allocation: a CUDA tensor (a CPU one for the host
+    entry point, host=True), of the grid's dtype, flat and large enough."""
     if not torch.is_tensor(t):
         raise TypeError(f"{what} must be a torch tensor")
+    if host != (t.device.type == "cpu"):
+        raise ValueError(f"{what} must be a {'host' if host else 'CUDA'} tensor (got {t.device})")
     if t.dtype != grid.torch_dtype:
         raise TypeError(f"{what} has dtype {t.dtype}, grid stores {grid.torch_dtype}")
     if t.dim() != 1 or not t.is_contiguous() or t.numel() < grid.alloc_elems:
@@ -283,12 +287,10 @@ class PW:
     def tendencies_host(self, u, v, w, su, sv, sw, scale=None, stream=None):
         """HOST tensors (pinned or pageable) in and out; synchronous."""
         g = self.grid
-        for name, t in (("u", u), ("v", v), ("w", w), ("su", su), ("sv", sv), ("sw", sw)):
-            if t.device.type != "cpu":
-                raise ValueError(f"{name} must be a host tensor")
         sp = _scale_arg(scale)
-        _check(lib().pw_tendencies_host(self.h, _ptr(u, g, "u"), _ptr(v, g, "v"), _ptr(w, g, "w"),
-                                        _ptr(su, g, "su"), _ptr(sv, g, "sv"), _ptr(sw, g, "sw"),
+        H = dict(host=True)
+        _check(lib().pw_tendencies_host(self.h, _ptr(u, g, "u", **H), _ptr(v, g, "v", **H), _ptr(w, g, "w", **H),
+                                        _ptr(su, g, "su", **H), _ptr(sv, g, "sv", **H), _ptr(sw, g, "sw", **H),
                                         sp[0] if sp else None, _stream_ptr(stream)), "pw_tendencies_host")
 
     def step(self, u, v, w, tmp_u, tmp_v, tmp_w, dt, nsteps, scale=None, stream=None):

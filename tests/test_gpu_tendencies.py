@@ -278,6 +278,19 @@ def test_host_path_matches_device_path(shape):
         assert np.array_equal(interior(x), interior(y))
 
 
+def test_binding_rejects_tensors_on_the_wrong_side():
+    """Host tensors never reach a device entry point (the GPU would fault on
+    the address) and device tensors never reach the host entry point."""
+    c, f, g, h, dev, outs = setup(64, 8, 5)
+    cpu = [t.cpu() for t in dev]
+    with pytest.raises(ValueError):
+        h.tendencies(*cpu, *outs)
+    with pytest.raises(ValueError):
+        h.step_to(*dev, *[t.cpu() for t in outs], 1.0)
+    with pytest.raises(ValueError):
+        h.tendencies_host(*dev, *[t.cpu() for t in outs])
+
+
 def test_error_norms_kernel():
     nx, ny, nz = 128, 12, 8
     c, f, g, h, dev, outs = setup(nx, ny, nz)
