@@ -29,7 +29,9 @@
  *   - Return a pw_status_t; on failure pw_last_error() (thread-local) holds a
  *     message.  Argument errors are detected on the host before any launch.
  *   - Field pointers are DEVICE pointers to caller-owned memory (for example
- *     torch tensors), unless an entry point says HOST.  The library never
+ *     torch tensors) of the handle's GPU, unless an entry point says HOST;
+ *     each is checked on the host (once per pointer, remembered by the
+ *     handle) and any other address gives PW_ERR_ARG.  The library never
  *     frees them.  Outputs must not alias inputs.
  *   - Calls are asynchronous on `stream` (a cudaStream_t cast to void*; NULL is
  *     the legacy default stream).  A kernel that gives up a bounded wait

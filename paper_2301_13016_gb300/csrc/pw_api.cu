@@ -86,6 +86,10 @@ struct pw_handle_s {
     AdjConfig adj_auto{0, 0, 0, 0};       // the shape in use; na == 0: not chosen yet
     MapCacheEntry maps[8];
     int map_next = 0;   // round-robin replacement
+    // field pointers already found to be device memory of this handle's GPU
+    static constexpr int kDevCache = 32;
+    const void* dev_ok[kDevCache] = {};
+    int dev_next = 0;
     // pw_tendencies_host staging and its copy / compute pipeline
     void* d_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};   // copy in, compute, copy out
@@ -151,6 +155,18 @@ bool pw::tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why) {
 
 bool pw::aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Device (or managed) memory of `device`?  A host address handed to a kernel
+// would fault the GPU, so every field pointer is checked on the host first.
+bool pw::is_device_ptr(const void* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of the query
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 // Tensor map of a field for a box of box_w x box_h elements, from the
 // handle's cache of recently encoded maps.
 static pw_status_t encode_map_box(pw_handle_t h, const void* ptr, int box_w, int box_h, CUtensorMap* out) {
@@ -201,6 +217,22 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return PW_OK;
+}
+
+// Every pointer in ps[0..n) is device memory of the handle's GPU (checked
+// once per pointer, then remembered).
+static pw_status_t check_device_ptrs(pw_handle_t h, const void* const* ps, int n) {
+    for (int a = 0; a < n; ++a) {
+        const void* p = ps[a];
+        bool known = false;
+        for (auto q : h->dev_ok) known = known || (q == p);
+        if (known) continue;
+        if (!is_device_ptr(p, h->device))
+            return fail(PW_ERR_ARG, "field pointer %p is not device memory of GPU %d", p, h->device);
+        h->dev_ok[h->dev_next] = p;
+        h->dev_next = (h->dev_next + 1) % pw_handle_s::kDevCache;
+    }
     return PW_OK;
 }
 
@@ -562,6 +594,11 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
         for (auto i : ins)
             if (o == i) return fail(PW_ERR_ARG, "an output aliases an input");
     if (su == sv || su == sw || sv == sw) return fail(PW_ERR_ARG, "outputs alias each other");
+    {
+        const void* all[6] = {u, v, w, su, sv, sw};
+        pw_status_t dst = check_device_ptrs(h, all, 6);
+        if (dst != PW_OK) return dst;
+    }
     if (scale)
         for (int q = 0; q < 6; ++q)
             if (!(scale[q] > 0.f) || !(scale[q] < 3.0e38f)) return fail(PW_ERR_ARG, "scales must be finite and > 0");
@@ -784,6 +821,8 @@ pw_status_t pw_step_to(pw_handle_t h, const void* u, const void* v, const void* 
     bool scaled = false;
     pw_status_t st = step_scales(scale, &sc, &scaled);
     if (st != PW_OK) return st;
+    st = check_device_ptrs(h, bufs, 6);
+    if (st != PW_OK) return st;
     bool use_tma = false;
     int ox = 0;
     st = step_kernel_choice(h, bufs, 6, &use_tma, &ox);
@@ -812,6 +851,8 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     Scales sc;
     bool scaled = false;
     pw_status_t sst = step_scales(scale, &sc, &scaled);
+    if (sst != PW_OK) return sst;
+    sst = check_device_ptrs(h, bufs, 6);
     if (sst != PW_OK) return sst;
     const GridDev g = to_dev(h->grid);
     CoefDev cf{h->tcx, h->tcy, h->d_tz};
@@ -891,6 +932,11 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
             if (o == i) return fail(PW_ERR_ARG, "an output aliases an input");
     if (gu == gv || gu == gw || gv == gw) return fail(PW_ERR_ARG, "outputs alias each other");
     if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return fail(PW_ERR_ARG, "alpha must be finite");
+    {
+        pw_status_t dst = check_device_ptrs(h, ins, 6);
+        if (dst == PW_OK) dst = check_device_ptrs(h, outs, 3);
+        if (dst != PW_OK) return dst;
+    }
     CoefDev cf{h->tcx, h->tcy, h->d_tz};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int ox = 0;
@@ -931,6 +977,11 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
 pw_status_t pw_fill_halo_periodic(pw_handle_t h, void* f, pw_stream_t stream) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!f) return fail(PW_ERR_ARG, "field pointer is NULL");
+    {
+        const void* p = f;
+        pw_status_t dst = check_device_ptrs(h, &p, 1);
+        if (dst != PW_OK) return dst;
+    }
     cudaError_t e = launch_fill_halo(h->grid.dtype, to_dev(h->grid), f, h->num_sms,
                                      reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "halo fill launch");
@@ -954,7 +1005,10 @@ pw_status_t pw_error_norms(pw_handle_t h, const void* test, float scale, const d
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!test || !ref || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
     if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
-    pw_status_t st = ensure_scratch(h);
+    const void* dp[2] = {test, ref};
+    pw_status_t st = check_device_ptrs(h, dp, 2);
+    if (st != PW_OK) return st;
+    st = ensure_scratch(h);
     if (st != PW_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_error_norms(h->grid.dtype, to_dev(h->grid), test, scale, ref, k0, k1, h->d_scratch,
@@ -971,7 +1025,10 @@ pw_status_t pw_weighted_dot(pw_handle_t h, const void* a, float sa, const void* 
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!a || !b || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
     if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
-    pw_status_t st = ensure_scratch(h);
+    const void* dp[2] = {a, b};
+    pw_status_t st = check_device_ptrs(h, dp, 2);
+    if (st != PW_OK) return st;
+    st = ensure_scratch(h);
     if (st != PW_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     double* d_wk = nullptr;

@@ -351,6 +351,8 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         }
     }
     if (!b->tables_ok || p != b->ptrs) {
+        for (const void* f : p)   // a host address would fault the GPU
+            if (!is_device_ptr(f, b->device)) return bfail(PW_ERR_ARG, "a field pointer is not device memory");
         // the pinned staging may still feed an earlier upload on this stream
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return internal_cuda_fail(e, "batch stream synchronize");

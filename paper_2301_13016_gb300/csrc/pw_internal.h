@@ -158,6 +158,8 @@ bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
 pw_status_t validate_grid(const pw_grid_t* g);
 bool tma_layout_ok(const pw_grid_t& g, int* ox_out, const char** why);
 bool aligned16(const void* p);
+// p is device (or managed) memory of the given GPU.
+bool is_device_ptr(const void* p, int device);
 pw_status_t encode_tensor_map(const pw_grid_t& g, const void* ptr, int lx, int ty, CUtensorMap* out, int nc = 4);
 // Same with an explicit box (box_w elements along x, box_h rows).
 pw_status_t encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out);

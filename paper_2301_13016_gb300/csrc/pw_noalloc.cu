@@ -57,6 +57,9 @@ extern "C" pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void* a, flo
     int num_sms = 0;
     if (!internal_handle_grid(h, &g, &num_sms)) return internal_fail(PW_ERR_ARG, "handle is NULL");
     if (!a || !b || !out) return internal_fail(PW_ERR_ARG, "a pointer is NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || !is_device_ptr(a, dev) || !is_device_ptr(b, dev))
+        return internal_fail(PW_ERR_ARG, "a field pointer is not device memory of the current GPU");
     if (k0 < 1 || k1 > g.nz || k0 > k1) return internal_fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
     if (g.nz + 2 > kNoallocMaxLevels)
         return internal_fail(PW_ERR_UNSUPPORTED,

@@ -289,6 +289,18 @@ def test_binding_rejects_tensors_on_the_wrong_side():
         h.step_to(*dev, *[t.cpu() for t in outs], 1.0)
     with pytest.raises(ValueError):
         h.tendencies_host(*dev, *[t.cpu() for t in outs])
+    # the C ABI checks too (pinned host memory: device-addressable, so even a
+    # missed check could not fault the GPU)
+    import ctypes
+    pinned = torch.zeros(g.alloc_elems, dtype=torch.float32).pin_memory()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    L = pwlib.lib()
+    assert L.pw_tendencies(h.h, *[P(t) for t in dev], P(outs[0]), P(outs[1]), P(pinned), None,
+                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == pwlib.PW_ERR_ARG
+    assert "not device memory" in L.pw_last_error().decode()
+    assert L.pw_fill_halo_periodic(h.h, P(pinned), None) == pwlib.PW_ERR_ARG
+    run(h, dev, outs)     # the handle still works
+    h.sync()
 
 
 def test_error_norms_kernel():
