@@ -191,7 +191,7 @@ def _ptr(t, grid, what, host=False):
     entry point, host=True), of the grid's dtype, flat and large enough."""
     if not torch.is_tensor(t):
         raise TypeError(f"{what} must be a torch tensor")
-    if host != (t.device.type == "cpu"):
+    if host == t.is_cuda:
         raise ValueError(f"{what} must be a {'host' if host else 'CUDA'} tensor (got {t.device})")
     if t.dtype != grid.torch_dtype:
         raise TypeError(f"{what} has dtype {t.dtype}, grid stores {grid.torch_dtype}")
