@@ -188,10 +188,13 @@ pw_status_t pw_tendencies(pw_handle_t h, const void *u, const void *v, const voi
  * pw_tendencies on HOST buffers (pageable or pinned) in the handle's layout:
  * copies u, v, w to device buffers the handle owns (allocated and zeroed on
  * first use), computes, copies su, sv, sw back, and returns when the results
- * are in host memory.  Per field, the contiguous span of levels 1..nz, from
- * element (1, 1-halo, 1-halo) to element (nz, ny+halo, nx+halo), travels
- * each way (the z-halo planes are never read); cells of that span outside
- * the interior come back as 0 in su, sv, sw.
+ * are in host memory.  What travels per field: levels 1..nz of u, v, w with
+ * their one-cell lateral halo (i = 0..nx+1, j = 0..ny+1: all the scheme
+ * reads), and the interior of levels 1..nz of su, sv, sw; row padding and
+ * cells outside those boxes do not travel, and host cells of su, sv, sw
+ * outside the interior are left as they are (as pw_tendencies leaves the
+ * device halos).  Levels are pipelined in chunks over copy-in, compute and
+ * copy-out streams.
  */
 pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, const void *w,
                                void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);

@@ -638,6 +638,33 @@ pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const voi
     return PW_OK;
 }
 
+// Copy the box i0..i0+ni-1, j0..j0+nj-1, levels k0..k1 of a field between
+// host and device buffers of the same layout: one 3D copy when a level is a
+// whole number of rows, else one 2D copy per level.  Only the box travels
+// (no row padding, no rows or columns outside it).
+static cudaError_t copy_box(const pw_grid_t& g, void* dst, const void* src, int i0, int ni, int j0, int nj, int k0,
+                            int k1, cudaMemcpyKind kind, cudaStream_t s) {
+    const size_t es = dtype_size(g.dtype);
+    const size_t pitch = (size_t)g.pitch_j * es;
+    auto at = [&](const void* base, int k) {
+        return (char*)base + (size_t)(g.origin + (long long)k * g.pitch_k + (long long)j0 * g.pitch_j + i0) * es;
+    };
+    if (g.pitch_k % g.pitch_j == 0) {
+        const size_t rows = (size_t)(g.pitch_k / g.pitch_j);
+        cudaMemcpy3DParms p = {};
+        p.srcPtr = make_cudaPitchedPtr(at(src, k0), pitch, (size_t)ni * es, rows);
+        p.dstPtr = make_cudaPitchedPtr(at(dst, k0), pitch, (size_t)ni * es, rows);
+        p.extent = make_cudaExtent((size_t)ni * es, (size_t)nj, (size_t)(k1 - k0 + 1));
+        p.kind = kind;
+        return cudaMemcpy3DAsync(&p, s);
+    }
+    for (int k = k0; k <= k1; ++k) {
+        cudaError_t e = cudaMemcpy2DAsync(at(dst, k), pitch, at(src, k), pitch, (size_t)ni * es, (size_t)nj, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
                                void* sw, const float* scale, pw_stream_t stream) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
@@ -655,13 +682,14 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
     cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
     const void* hin[3] = {u, v, w};
     void* hout[3] = {su, sv, sw};
-    // contiguous element span of levels a..b (full padded planes)
-    auto span = [&](int a, int b, size_t* off, size_t* len) {
-        const long long lo = g.origin + (long long)a * g.pitch_k + (long long)(1 - g.halo) * g.pitch_j + 1 - g.halo;
-        const long long hi = g.origin + (long long)b * g.pitch_k + (long long)(g.ny + g.halo) * g.pitch_j + g.nx +
-                             g.halo + 1;
-        *off = (size_t)lo * es;
-        *len = (size_t)(hi - lo) * es;
+    // what travels: levels a..b of the inputs with their one-cell lateral
+    // halo (all the scheme reads), and the interior of levels a..b of the
+    // outputs
+    auto copy_in = [&](int q, int a, int b, cudaStream_t s) {
+        return copy_box(g, h->d_stage[q], hin[q], 0, g.nx + 2, 0, g.ny + 2, a, b, cudaMemcpyHostToDevice, s);
+    };
+    auto copy_out = [&](int q, int a, int b, cudaStream_t s) {
+        return copy_box(g, hout[q], h->d_stage[3 + q], 1, g.nx, 1, g.ny, a, b, cudaMemcpyDeviceToHost, s);
     };
 
     int ox = 0;
@@ -670,19 +698,11 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
     for (auto p : h->d_stage) ptrs_ok = ptrs_ok && aligned16(p);
     const bool pipelined = h->kernel_kind != 1 && ptrs_ok && tma_layout_ok(g, &ox, &why) && g.nz >= 8;
     if (!pipelined) {   // one copy in, one launch, one copy out
-        size_t off, len;
-        span(1, g.nz, &off, &len);
-        for (int q = 0; q < 3; ++q)
-            PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len, cudaMemcpyHostToDevice,
-                                    us),
-                    "pw_tendencies_host input copy");
+        for (int q = 0; q < 3; ++q) PW_CUDA(copy_in(q, 1, g.nz, us), "pw_tendencies_host input copy");
         pw_status_t st = pw_tendencies(h, h->d_stage[0], h->d_stage[1], h->d_stage[2], h->d_stage[3], h->d_stage[4],
                                        h->d_stage[5], scale, stream);
         if (st != PW_OK) return st;
-        for (int q = 0; q < 3; ++q)
-            PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len,
-                                    cudaMemcpyDeviceToHost, us),
-                    "pw_tendencies_host output copy");
+        for (int q = 0; q < 3; ++q) PW_CUDA(copy_out(q, 1, g.nz, us), "pw_tendencies_host output copy");
         PW_CUDA(cudaStreamSynchronize(us), "pw_tendencies_host synchronize");
         return PW_OK;
     }
@@ -723,12 +743,8 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         const int ke = (int)(((long long)(c + 1) * g.nz) / C);
         const int need = std::min(ke + 1, g.nz);
         if (need > copied) {
-            size_t off, len;
-            span(copied + 1, need, &off, &len);
             for (int q = 0; q < 3; ++q)
-                PW_CUDA(cudaMemcpyAsync((char*)h->d_stage[q] + off, (const char*)hin[q] + off, len,
-                                        cudaMemcpyHostToDevice, h->hs[0]),
-                        "pw_tendencies_host input copy");
+                PW_CUDA(copy_in(q, copied + 1, need, h->hs[0]), "pw_tendencies_host input copy");
             copied = need;
         }
         PW_CUDA(cudaEventRecord(h->ev_in[c], h->hs[0]), "pipeline event");
@@ -739,12 +755,7 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         if (e != cudaSuccess) return cuda_fail(e, "TMA tendency kernel launch");
         PW_CUDA(cudaEventRecord(h->ev_comp[c], h->hs[1]), "pipeline event");
         PW_CUDA(cudaStreamWaitEvent(h->hs[2], h->ev_comp[c], 0), "pipeline wait");
-        size_t off, len;
-        span(kb, ke, &off, &len);
-        for (int q = 0; q < 3; ++q)
-            PW_CUDA(cudaMemcpyAsync((char*)hout[q] + off, (const char*)h->d_stage[3 + q] + off, len,
-                                    cudaMemcpyDeviceToHost, h->hs[2]),
-                    "pw_tendencies_host output copy");
+        for (int q = 0; q < 3; ++q) PW_CUDA(copy_out(q, kb, ke, h->hs[2]), "pw_tendencies_host output copy");
     }
     h->last_kernel = 2;
     PW_CUDA(cudaEventRecord(h->ev_end, h->hs[2]), "pipeline event");

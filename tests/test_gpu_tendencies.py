@@ -264,18 +264,31 @@ def test_mirror_antisymmetry_on_gpu():
     assert np.abs(interior(b[2]) - a[2][1:-1, 1:-1, ic]).max() <= 1e-6 * sc
 
 
-@pytest.mark.parametrize("shape", [(256, 20, 9), (128, 16, 64), (36, 8, 5)], ids=["2chunks", "8chunks", "unpipelined"])
-def test_host_path_matches_device_path(shape):
+@pytest.mark.parametrize("shape,layout", [((256, 20, 9), None), ((128, 16, 64), None), ((36, 8, 5), None),
+                                          ((64, 8, 9), (72, 72 * 10 + 8, 3))],
+                         ids=["2chunks", "8chunks", "unpipelined", "level_pitch_not_whole_rows"])
+def test_host_path_matches_device_path(shape, layout):
+    """The host path gives the device path's bits on the interior and leaves
+    every other host cell of the outputs as it was (3D box copies, or 2D
+    copies per level when a level is not a whole number of rows)."""
     nx, ny, nz = shape
-    c, f, g, h, dev, outs = setup(nx, ny, nz)
+    grid = None
+    if layout:
+        pj, pk, origin = layout
+        grid = pwlib.Grid(nx, ny, nz, pitch_j=pj, pitch_k=pk, origin=origin)
+    c, f, g, h, dev, outs = setup(nx, ny, nz, grid=grid)
     run(h, dev, outs)
     a = dense_out(g, outs)
     hin = [t.cpu().pin_memory() for t in dev]
-    hout = [torch.zeros(g.alloc_elems, dtype=torch.float32).pin_memory() for _ in range(3)]
+    hout = [torch.full((g.alloc_elems,), 7.0, dtype=torch.float32).pin_memory() for _ in range(3)]
     h.tendencies_host(*hin, *hout)
+    assert h.last_kernel == 2
     b = [g.to_dense(t).numpy() for t in hout]
-    for x, y in zip(a, b):
+    for x, y, t in zip(a, b, hout):
         assert np.array_equal(interior(x), interior(y))
+        inside = torch.zeros(g.alloc_elems, dtype=torch.bool)
+        g.view(inside)[1:-1, 1:-1, 1:-1] = True
+        assert torch.all(t[~inside] == 7.0)
 
 
 def test_binding_rejects_tensors_on_the_wrong_side():
