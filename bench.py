@@ -772,6 +772,52 @@ def form_latency64(args):
                {"dtype": "f32", "higher_is_better": False, "shapes": res, "gcells_at_best": g.cells / best / 1e3})
 
 
+def _torch_cudart():
+    """The CUDA runtime library torch loaded (pitched copies, which torch
+    does not expose, are issued through it on torch's streams), or None."""
+    import ctypes
+    torch.cuda.init()
+    try:
+        with open("/proc/self/maps") as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 6 and os.path.basename(parts[-1]).startswith("libcudart.so"):
+                    return ctypes.CDLL(parts[-1])
+    except OSError:
+        pass
+    return None
+
+
+def _pitched_box_copies(rt, g, dst, src, i0, ni, j0, nj, chunks, kind, stream):
+    """Issue 3D copies of the box i0..i0+ni-1, j0..j0+nj-1 of each level chunk
+    (k0, k1) between two flat FP32 allocations of layout g, as the host path
+    copies them (cudaMemcpy3DAsync; kind 1 = host to device, 2 = device to
+    host)."""
+    import ctypes
+
+    class Pos(ctypes.Structure):
+        _fields_ = [("x", ctypes.c_size_t), ("y", ctypes.c_size_t), ("z", ctypes.c_size_t)]
+
+    class PPtr(ctypes.Structure):
+        _fields_ = [("ptr", ctypes.c_void_p), ("pitch", ctypes.c_size_t), ("xsize", ctypes.c_size_t),
+                    ("ysize", ctypes.c_size_t)]
+
+    class Parms(ctypes.Structure):
+        _fields_ = [("srcArray", ctypes.c_void_p), ("srcPos", Pos), ("srcPtr", PPtr), ("dstArray", ctypes.c_void_p),
+                    ("dstPos", Pos), ("dstPtr", PPtr), ("extent", Pos), ("kind", ctypes.c_int)]
+
+    rows = g.pitch_k // g.pitch_j
+    for k0, k1 in chunks:
+        off = 4 * (g.origin + k0 * g.pitch_k + j0 * g.pitch_j + i0)
+        p = Parms()
+        p.srcPtr = PPtr(src.data_ptr() + off, 4 * g.pitch_j, 4 * ni, rows)
+        p.dstPtr = PPtr(dst.data_ptr() + off, 4 * g.pitch_j, 4 * ni, rows)
+        p.extent = Pos(4 * ni, nj, k1 - k0 + 1)
+        p.kind = kind
+        if rt.cudaMemcpy3DAsync(ctypes.byref(p), ctypes.c_void_p(stream.cuda_stream)) != 0:
+            raise RuntimeError("cudaMemcpy3DAsync failed")
+
+
 def form_hostlink(args):
     """The bound of the end-to-end number: the host link.  Measures the link's
     rate with plain copies of levels 1..nz of three fields between pinned
@@ -849,14 +895,25 @@ def form_hostlink(args):
         for q in range(3):
             torch.add(dout[q][lo:hi], 0.0, out=hv_out[q][lo:hi])
 
+    # the host path's own copies without the kernel: pitched boxes per 4-level
+    # chunk (inputs with a one-cell halo in, output interiors out)
+    rt = _torch_cudart()
+    chunks = [(1 + c * nz // 16, (c + 1) * nz // 16) for c in range(16)]
+
+    def boxes_both():
+        for q in range(3):
+            _pitched_box_copies(rt, g, din[q], hin[q], 0, nx + 2, 0, ny + 2, chunks, 1, s_in)
+            _pitched_box_copies(rt, g, hout[q], dout[q], 1, nx, 1, ny, chunks, 2, s_out)
+
     reps = max(2, min(args.steps, 10))
     t_in, t_out = wall(h2d, reps), wall(d2h, reps)
     t_both = wall(lambda: (h2d(), d2h()), reps)
+    t_boxes = wall(boxes_both, reps) if rt is not None else None
     t_in3, t_out3 = wall(h2d3, reps), wall(d2h3, reps)
     t_smr, t_smw = wall(sm_read, reps), wall(sm_write, reps)
     t_path = wall(lambda: h.tendencies_host(*hin, *hout), reps)
     val = g.cells / t_path / 1e9
-    t_bound = max(gb_in, gb_out) / (gb / t_both)
+    t_bound = t_boxes if t_boxes is not None else max(gb_in, gb_out) / (gb / t_both)
     _form_line(args, "hostlink", "PW tendencies end to end through host buffers, against the host-link bound", val,
                "Gcell/s", {"workload": f"{nx}x{ny}x{nz} FP32, pinned host buffers, {gb_in:.3f} GB in and "
                                        f"{gb_out:.3f} GB out per call"},
@@ -865,6 +922,8 @@ def form_hostlink(args):
                              "h2d_three_streams": gb / t_in3, "d2h_three_streams": gb / t_out3,
                              "sm_loads_from_host": gb / t_smr, "sm_stores_to_host": gb / t_smw},
                 "plain_copies_gb_each_way": gb, "plain_copies_both_ms": t_both * 1e3,
+                "box_copies_both_ms": t_boxes * 1e3 if t_boxes is not None else None,
+                "box_copies_gbs_each_way": gb_in / t_boxes if t_boxes is not None else None,
                 "bound_ms": t_bound * 1e3, "bound_gcells": g.cells / t_bound / 1e9,
                 "frac_of_link_bound": t_bound / t_path, "h2d_bytes_per_step": int(gb_in * 1e9),
                 "d2h_bytes_per_step": int(gb_out * 1e9)})

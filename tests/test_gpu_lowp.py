@@ -205,7 +205,7 @@ def test_automatic_launch_shapes():
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_host_path_16bit_matches_device_path(dtype):
     """pw_tendencies_host with 16-bit storage (the packed two-row shape,
-    pipelined in 8-level chunks; FP16 with scales) gives the device path's
+    pipelined in 4-level chunks; FP16 with scales) gives the device path's
     bits."""
     nx, ny, nz = 256, 20, 64
     c = inputs.make_coeffs(nz)

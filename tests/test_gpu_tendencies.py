@@ -266,7 +266,7 @@ def test_mirror_antisymmetry_on_gpu():
 
 @pytest.mark.parametrize("shape,layout", [((256, 20, 9), None), ((128, 16, 64), None), ((36, 8, 5), None),
                                           ((64, 8, 9), (72, 72 * 10 + 8, 3))],
-                         ids=["2chunks", "8chunks", "unpipelined", "level_pitch_not_whole_rows"])
+                         ids=["2chunks", "16chunks", "unpipelined", "level_pitch_not_whole_rows"])
 def test_host_path_matches_device_path(shape, layout):
     """The host path gives the device path's bits on the interior and leaves
     every other host cell of the outputs as it was (3D box copies, or 2D
