@@ -905,10 +905,18 @@ def form_hostlink(args):
             _pitched_box_copies(rt, g, din[q], hin[q], 0, nx + 2, 0, ny + 2, chunks, 1, s_in)
             _pitched_box_copies(rt, g, hout[q], dout[q], 1, nx, 1, ny, chunks, 2, s_out)
 
+    s6 = [torch.cuda.Stream() for _ in range(6)]
+
+    def boxes_six_streams():   # one stream per field and direction
+        for q in range(3):
+            _pitched_box_copies(rt, g, din[q], hin[q], 0, nx + 2, 0, ny + 2, chunks, 1, s6[q])
+            _pitched_box_copies(rt, g, hout[q], dout[q], 1, nx, 1, ny, chunks, 2, s6[3 + q])
+
     reps = max(2, min(args.steps, 10))
     t_in, t_out = wall(h2d, reps), wall(d2h, reps)
     t_both = wall(lambda: (h2d(), d2h()), reps)
     t_boxes = wall(boxes_both, reps) if rt is not None else None
+    t_boxes6 = wall(boxes_six_streams, reps) if rt is not None else None
     t_in3, t_out3 = wall(h2d3, reps), wall(d2h3, reps)
     t_smr, t_smw = wall(sm_read, reps), wall(sm_write, reps)
     t_path = wall(lambda: h.tendencies_host(*hin, *hout), reps)
@@ -924,6 +932,7 @@ def form_hostlink(args):
                 "plain_copies_gb_each_way": gb, "plain_copies_both_ms": t_both * 1e3,
                 "box_copies_both_ms": t_boxes * 1e3 if t_boxes is not None else None,
                 "box_copies_gbs_each_way": gb_in / t_boxes if t_boxes is not None else None,
+                "box_copies_six_streams_ms": t_boxes6 * 1e3 if t_boxes6 is not None else None,
                 "bound_ms": t_bound * 1e3, "bound_gcells": g.cells / t_bound / 1e9,
                 "frac_of_link_bound": t_bound / t_path, "h2d_bytes_per_step": int(gb_in * 1e9),
                 "d2h_bytes_per_step": int(gb_out * 1e9)})
