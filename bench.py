@@ -194,9 +194,10 @@ class ClockSampler:
 
 
 def cpu_baseline(w, budget_s=10.0, slab=None):
-    """The CPU oracle (FP64 plain C loop nest, one thread) on slabs of the
-    same workload: nx x 128 x nz grids, repeated until about budget_s seconds
-    of CPU work.  With `slab` (rows 1..128 of the benchmark's own inputs, with
+    """The CPU oracle (plain C loop nest, unchanged) on slabs of the same
+    workload: nx x 128 x nz grids, repeated until about budget_s seconds of
+    CPU work in all: FP64 on every host core at once (the value), and beside
+    it FP32 on every core and FP64 / FP32 on one thread.  With `slab` (rows 1..128 of the benchmark's own inputs, with
     their halo rows, and the GPU's FP32 and BF16-storage source terms on those
     rows) the slab is the sample, and its first oracle result is also the
     reference the GPU outputs are checked against: max|err| / max|ref| per
@@ -230,17 +231,18 @@ def cpu_baseline(w, budget_s=10.0, slab=None):
             reps += 1
         return cells / t_used / 1e9, reps, t_used
 
-    def all_cores(budget):
+    def all_cores(budget, precision="f64"):
         # the same single-thread oracle on every host core at once: its C
         # loop runs outside the interpreter lock, one call per thread
         import concurrent.futures as cf
         n = len(os.sched_getaffinity(0))
+        args = f if precision == "f64" else [x.astype(np.float32) for x in f]
         deadline = time.perf_counter() + budget
 
         def worker(_):
             done = 0
             while time.perf_counter() < deadline:
-                oracle.tendencies(*f, c)
+                oracle.tendencies(*args, c, precision=precision)
                 done += 1
             return done
         t = time.perf_counter()
@@ -248,12 +250,14 @@ def cpu_baseline(w, budget_s=10.0, slab=None):
             calls = sum(ex.map(worker, range(n)))
         return calls * slab_cells / (time.perf_counter() - t) / 1e9, n, calls
 
-    v64, reps, t_used = single("f64", budget_s * 0.5)
-    v32, reps32, t32 = single("f32", budget_s * 0.2)
+    v64, reps, t_used = single("f64", budget_s * 0.4)
+    v32, reps32, t32 = single("f32", budget_s * 0.15)
     vall, n, calls = all_cores(budget_s * 0.3)
+    vall32, _, calls32 = all_cores(budget_s * 0.15, "f32")
     out = {"value": vall, "unit": "Gcell/s", "cores": n, "kind": "oracle",
            "sample": f"FP64 oracle on ({nx}x{ny}x{nz}) slabs of the same workload: {calls} calls spread over "
                      f"{n} threads (one per host core) for {budget_s * 0.3:.1f} s",
+           "all_cores_f32": vall32, "all_cores_f32_calls": calls32,
            "single_thread_f64": v64, "single_thread_f32": v32,
            "single_thread_sample": f"{reps} FP64 calls in {t_used:.1f} s, {reps32} FP32 calls in {t32:.1f} s"}
     if parity is not None:
