@@ -265,15 +265,17 @@ def test_mirror_antisymmetry_on_gpu():
 
 
 @pytest.mark.parametrize("shape,layout", [((256, 20, 9), None), ((128, 16, 64), None), ((36, 8, 5), None),
-                                          ((64, 8, 9), (72, 72 * 10 + 8, 3))],
-                         ids=["2chunks", "16chunks", "unpipelined", "level_pitch_not_whole_rows"])
+                                          ((64, 8, 9), (72, 72 * 10 + 8, 3)), ((128, 12, 10), "halo2")],
+                         ids=["2chunks", "16chunks", "unpipelined", "level_pitch_not_whole_rows", "halo2"])
 def test_host_path_matches_device_path(shape, layout):
     """The host path gives the device path's bits on the interior and leaves
     every other host cell of the outputs as it was (3D box copies, or 2D
     copies per level when a level is not a whole number of rows)."""
     nx, ny, nz = shape
     grid = None
-    if layout:
+    if layout == "halo2":
+        grid = pwlib.Grid(nx, ny, nz, halo=2)
+    elif layout:
         pj, pk, origin = layout
         grid = pwlib.Grid(nx, ny, nz, pitch_j=pj, pitch_k=pk, origin=origin)
     c, f, g, h, dev, outs = setup(nx, ny, nz, grid=grid)
@@ -287,7 +289,8 @@ def test_host_path_matches_device_path(shape, layout):
     for x, y, t in zip(a, b, hout):
         assert np.array_equal(interior(x), interior(y))
         inside = torch.zeros(g.alloc_elems, dtype=torch.bool)
-        g.view(inside)[1:-1, 1:-1, 1:-1] = True
+        hh = g.halo
+        g.view(inside)[1:-1, hh:hh + ny, hh:hh + nx] = True
         assert torch.all(t[~inside] == 7.0)
 
 
