@@ -217,3 +217,75 @@ def test_abs_terms_bounds_and_pins():
     s32 = tend32(u, v, w, c)
     for x, y, ai in zip(s32, s, a):
         assert np.all(np.abs(x - y) <= 16 * 2.0 ** -24 * ai + 1e-300)
+
+
+def _scatter_face_by_face(u, v, w, c):
+    """The scheme restated face by face, the way a flux-form code scatters:
+    across each face between cells A and B = A + e, with advecting pair sum P
+    on that face, cell B receives +coef * phi(A) * P and cell A receives
+    -coef' * phi(B) * P (Sec. 2.2's terms c * a * (b + d), grouped by face
+    instead of by output cell).  Only cells where the scheme has outputs
+    receive: su, sv at levels 2..nz (the upper vertical term up to nz-1), sw
+    at 2..nz-1, interior columns.  An index cross-check of the oracle's
+    gather loops (the same terms, in a different arrangement), not an
+    independent pin."""
+    nz, ny, nx = u.shape[0] - 2, u.shape[1] - 2, u.shape[2] - 2
+    su, sv, sw = np.zeros(u.shape), np.zeros(u.shape), np.zeros(u.shape)
+    inside = lambda j, i: 1 <= j <= ny and 1 <= i <= nx
+
+    def face(s, phi, coef_b, coef_a, P, A, B, ok_a, ok_b):
+        if ok_b and inside(*B[1:]):
+            s[B] += coef_b * phi[A] * P
+        if ok_a and inside(*A[1:]):
+            s[A] -= coef_a * phi[B] * P
+
+    for k in range(1, nz + 1):
+        uv_k = 2 <= k <= nz
+        w_k = 2 <= k <= nz - 1
+        for j in range(0, ny + 2):
+            for i in range(1, nx + 2):           # x faces between i-1 and i
+                A, B = (k, j, i - 1), (k, j, i)
+                face(su, u, c.tcx, c.tcx, u[k, j, i - 1] + u[k, j, i], A, B, uv_k, uv_k)
+                if j <= ny:
+                    face(sv, v, c.tcx, c.tcx, u[k, j, i - 1] + u[k, j + 1, i - 1], A, B, uv_k, uv_k)
+                if k <= nz - 1:
+                    face(sw, w, c.tcx, c.tcx, u[k, j, i - 1] + u[k + 1, j, i - 1], A, B, w_k, w_k)
+        for j in range(1, ny + 2):               # y faces between j-1 and j
+            for i in range(0, nx + 2):
+                A, B = (k, j - 1, i), (k, j, i)
+                if i <= nx:
+                    face(su, u, c.tcy, c.tcy, v[k, j - 1, i] + v[k, j - 1, i + 1], A, B, uv_k, uv_k)
+                face(sv, v, c.tcy, c.tcy, v[k, j - 1, i] + v[k, j, i], A, B, uv_k, uv_k)
+                if k <= nz - 1:
+                    face(sw, w, c.tcy, c.tcy, v[k, j - 1, i] + v[k + 1, j - 1, i], A, B, w_k, w_k)
+    for k in range(2, nz + 1):                   # z faces between k-1 and k
+        for j in range(0, ny + 2):
+            for i in range(0, nx + 2):
+                A, B = (k - 1, j, i), (k, j, i)
+                up_ok = 2 <= k - 1 <= nz - 1     # the upper vertical term of level k-1
+                if i <= nx:
+                    face(su, u, c.tzc1[k], c.tzc2[k - 1], w[k - 1, j, i] + w[k - 1, j, i + 1], A, B, up_ok, True)
+                if j <= ny:
+                    face(sv, v, c.tzc1[k], c.tzc2[k - 1], w[k - 1, j, i] + w[k - 1, j + 1, i], A, B, up_ok, True)
+                face(sw, w, c.tzd1[k], c.tzd2[k - 1], w[k - 1, j, i] + w[k, j, i], A, B, up_ok, k <= nz - 1)
+    return su, sv, sw
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_face_by_face_scatter_on_4cubed_dyadic_grids(seed):
+    """4 x 4 x 4 interior with dyadic values (multiples of 1/4 in -2..2) and
+    dyadic coefficients (multiples of 1/8): every product and sum is exact in
+    FP64, so the scatter restatement and the oracle agree bit for bit."""
+    rng = np.random.default_rng(seed)
+    n = 4
+    shape = (n + 2, n + 2, n + 2)
+    u, v, w = (rng.integers(-8, 9, size=shape) / 4.0 for _ in range(3))
+    c = inputs.make_coeffs(n)
+    c.tcx, c.tcy = 0.25, 0.5
+    for name in ("tzc1", "tzc2", "tzd1", "tzd2"):
+        setattr(c, name, rng.integers(1, 9, size=n + 2) / 8.0)
+    ref = _scatter_face_by_face(u, v, w, c)
+    got = tend64(u, v, w, c)
+    for g, r in zip(got, ref):
+        assert np.array_equal(g[1:-1, 1:-1, 1:-1], r[1:-1, 1:-1, 1:-1])
+        assert np.any(r[1:-1, 1:-1, 1:-1] != 0)
