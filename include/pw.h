@@ -352,7 +352,8 @@ pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void *a, float sa, cons
  * CUDA graph.  The paper scales its design by decomposing the problem into
  * independent compute units that each own part of the grid (Sec. 5); here a
  * unit is a whole grid and every (grid, tile) pair is a work item, taken
- * longest first from an atomic counter by one k-march CTA per SM slot.
+ * from an atomic counter by one k-march CTA per SM slot: the deepest grids
+ * first, each grid's tiles together in raster order.
  * Every grid's layout must qualify for the k-march kernel (pw_grid_default
  * layouts with nx a multiple of 4 do), else PW_ERR_UNSUPPORTED.
  */

@@ -167,8 +167,8 @@ static void drop_graph(pw_batch_t b) {
     b->graph = nullptr;
 }
 
-// Work items for the current tile shape, longest first (levels, then width).
-// Work order: grids longest first by depth (nz), each grid's tiles together
+// Work items for the current tile shape.
+// Work order: the deepest grids first (nz), each grid's tiles together
 // in raster order (x fastest), so a tile's neighbours start at about the same
 // time and their shared halo rows and columns come from L2.  Measured on the
 // 512-grid batch: 222 Gcell/s, against 212 when the tile width was part of
