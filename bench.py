@@ -391,14 +391,26 @@ def run_ours(args, rank, world, local):
     del dev, outs
     torch.cuda.empty_cache()
     h.tendencies_host(*hin, *hout, stream=stream)          # warm (allocates staging)
+    # one call at a time (each returns with its results in host memory) ...
     barrier(world)
     t = time.perf_counter()
     for _ in range(args.e2e_steps):
         h.tendencies_host(*hin, *hout, stream=stream)
+    sync_s = max_over_ranks(time.perf_counter() - t, world)
+    # ... and the steps back to back through the asynchronous entry point, one
+    # sync at the end: a step's inputs travel while the last step's outputs
+    # come back (the reported value)
+    barrier(world)
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        h.tendencies_host_async(*hin, *hout, stream=stream)
+    h.sync(stream)
     e2e_s = max_over_ranks(time.perf_counter() - t, world)
     # what the host path moves: the inputs with their one-cell halo, the
     # interior of the outputs (levels 1..nz)
     e2e = {"value": whole_job_rate(cells * args.e2e_steps, world, e2e_s) / 1e9, "unit": "Gcell/s",
+           "api": "pw_tendencies_host_async, steps back to back, one sync",
+           "one_call_at_a_time": whole_job_rate(cells * args.e2e_steps, world, sync_s) / 1e9,
            "h2d_bytes_per_step": 3 * 4 * (nx + 2) * (ny + 2) * nz, "d2h_bytes_per_step": 3 * 4 * cells,
            "steps": args.e2e_steps}
 
@@ -924,6 +936,11 @@ def form_hostlink(args):
     t_in3, t_out3 = wall(h2d3, reps), wall(d2h3, reps)
     t_smr, t_smw = wall(sm_read, reps), wall(sm_write, reps)
     t_path = wall(lambda: h.tendencies_host(*hin, *hout), reps)
+
+    def path_async(n=4):   # n steps back to back, one wait
+        for _ in range(n):
+            h.tendencies_host_async(*hin, *hout)
+    t_async = wall(path_async, reps) / 4
     val = g.cells / t_path / 1e9
     t_bound = t_boxes if t_boxes is not None else max(gb_in, gb_out) / (gb / t_both)
     _form_line(args, "hostlink", "PW tendencies end to end through host buffers, against the host-link bound", val,
@@ -938,7 +955,9 @@ def form_hostlink(args):
                 "box_copies_gbs_each_way": gb_in / t_boxes if t_boxes is not None else None,
                 "box_copies_six_streams_ms": t_boxes6 * 1e3 if t_boxes6 is not None else None,
                 "bound_ms": t_bound * 1e3, "bound_gcells": g.cells / t_bound / 1e9,
-                "frac_of_link_bound": t_bound / t_path, "h2d_bytes_per_step": int(gb_in * 1e9),
+                "frac_of_link_bound": t_bound / t_path,
+                "async_back_to_back_ms_per_step": t_async * 1e3, "async_back_to_back_gcells": g.cells / t_async / 1e9,
+                "async_frac_of_link_bound": t_bound / t_async, "h2d_bytes_per_step": int(gb_in * 1e9),
                 "d2h_bytes_per_step": int(gb_out * 1e9)})
 
 

@@ -200,6 +200,19 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
                                void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
 
 /*
+ * pw_tendencies_host that returns once the work is enqueued: the results are
+ * in host memory once `stream` reaches the point after the call (it waits for
+ * the call's last copy), for example after pw_sync(h, stream).  Until then
+ * the host inputs must stay unchanged and the host outputs untouched.  Calls
+ * on one handle may follow each other without waiting: a call's inputs travel
+ * while the previous call's outputs come back (with pinned host memory; with
+ * pageable memory the copies are synchronous).  Same arguments and results
+ * as pw_tendencies_host.
+ */
+pw_status_t pw_tendencies_host_async(pw_handle_t h, const void *u, const void *v, const void *w,
+                                     void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
+
+/*
  * Advance the advection-only system nsteps forward-Euler steps,
  * q <- q + dt * s(q) for q = (u, v, w), with s the PW source terms (the scheme
  * is evaluated every model timestep, Sec. 2.2), doubly periodic lateral

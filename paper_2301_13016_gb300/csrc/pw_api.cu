@@ -94,7 +94,7 @@ struct pw_handle_s {
     void* d_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};   // copy in, compute, copy out
     static constexpr int kMaxChunks = 32;
-    cudaEvent_t ev_in[kMaxChunks] = {}, ev_comp[kMaxChunks] = {};
+    cudaEvent_t ev_in[kMaxChunks] = {}, ev_comp[kMaxChunks] = {}, ev_out[kMaxChunks] = {};
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
     // validation scratch: 4*(nblocks+1) doubles + wk (nz+2 doubles)
     double* d_scratch = nullptr;
@@ -426,11 +426,14 @@ pw_status_t pw_create(const pw_grid_t* grid, const pw_coeffs_t* coeffs, pw_handl
 
 pw_status_t pw_destroy(pw_handle_t h) {
     if (!h) return PW_OK;
+    for (auto& st : h->hs)   // an asynchronous host call may still be running
+        if (st) cudaStreamSynchronize(st);
     for (auto& st : h->hs)
         if (st) cudaStreamDestroy(st);
     for (int c = 0; c < pw_handle_s::kMaxChunks; ++c) {
         if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
         if (h->ev_comp[c]) cudaEventDestroy(h->ev_comp[c]);
+        if (h->ev_out[c]) cudaEventDestroy(h->ev_out[c]);
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     if (h->ev_end) cudaEventDestroy(h->ev_end);
@@ -673,8 +676,10 @@ static cudaError_t copy_box(const pw_grid_t& g, void* dst, const void* src, int 
     return cudaSuccess;
 }
 
-pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
-                               void* sw, const float* scale, pw_stream_t stream) {
+// The host path; wait = return once the results are in host memory, else
+// once the work is enqueued (the caller's stream waits for its last copy).
+static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
+                                   void* sw, const float* scale, pw_stream_t stream, bool wait) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!u || !v || !w || !su || !sv || !sw) return fail(PW_ERR_ARG, "a field pointer is NULL");
     const pw_grid_t& g = h->grid;
@@ -711,18 +716,25 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
                                        h->d_stage[5], scale, stream);
         if (st != PW_OK) return st;
         for (int q = 0; q < 3; ++q) PW_CUDA(copy_out(q, 1, g.nz, us), "pw_tendencies_host output copy");
-        PW_CUDA(cudaStreamSynchronize(us), "pw_tendencies_host synchronize");
+        if (wait) PW_CUDA(cudaStreamSynchronize(us), "pw_tendencies_host synchronize");
         return PW_OK;
     }
 
     // Pipelined over k chunks: chunk c's input planes travel on stream 0
     // while chunk c-1 is computed on stream 1 and chunk c-2's outputs travel
     // back on stream 2 (the two copy directions and the kernels overlap).
+    // Calls on one handle share the staging buffers, and a call may start
+    // before the previous one has finished (the asynchronous form): chunk c's
+    // input copy first waits for the previous call's kernels that read those
+    // levels (chunks up to c+2), and chunk c's kernel for the previous call's
+    // copy out of chunk c, so one call's inputs travel while the last one's
+    // outputs come back.
     for (auto& st : h->hs)
         if (!st) PW_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "pipeline stream");
     for (int c = 0; c < pw_handle_s::kMaxChunks; ++c) {
         if (!h->ev_in[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming), "pipeline event");
         if (!h->ev_comp[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_comp[c], cudaEventDisableTiming), "pipeline event");
+        if (!h->ev_out[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_out[c], cudaEventDisableTiming), "pipeline event");
     }
     if (!h->ev_start) PW_CUDA(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming), "pipeline event");
     if (!h->ev_end) PW_CUDA(cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming), "pipeline event");
@@ -751,12 +763,15 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         const int ke = (int)(((long long)(c + 1) * g.nz) / C);
         const int need = std::min(ke + 1, g.nz);
         if (need > copied) {
+            // (an event not recorded yet, as on a handle's first call, is no wait)
+            PW_CUDA(cudaStreamWaitEvent(h->hs[0], h->ev_comp[std::min(c + 2, C - 1)], 0), "pipeline wait");
             for (int q = 0; q < 3; ++q)
                 PW_CUDA(copy_in(q, copied + 1, need, h->hs[0]), "pw_tendencies_host input copy");
             copied = need;
         }
         PW_CUDA(cudaEventRecord(h->ev_in[c], h->hs[0]), "pipeline event");
         PW_CUDA(cudaStreamWaitEvent(h->hs[1], h->ev_in[c], 0), "pipeline wait");
+        PW_CUDA(cudaStreamWaitEvent(h->hs[1], h->ev_out[c], 0), "pipeline wait");
         cfg.seg0 = c;
         cudaError_t e = launch_tend_tma(g.dtype, gd, ox, maps, h->d_stage[3], h->d_stage[4], h->d_stage[5], sc,
                                         cf, h->d_err, cfg, h->hs[1]);
@@ -764,12 +779,23 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, cons
         PW_CUDA(cudaEventRecord(h->ev_comp[c], h->hs[1]), "pipeline event");
         PW_CUDA(cudaStreamWaitEvent(h->hs[2], h->ev_comp[c], 0), "pipeline wait");
         for (int q = 0; q < 3; ++q) PW_CUDA(copy_out(q, kb, ke, h->hs[2]), "pw_tendencies_host output copy");
+        PW_CUDA(cudaEventRecord(h->ev_out[c], h->hs[2]), "pipeline event");
     }
     h->last_kernel = 2;
     PW_CUDA(cudaEventRecord(h->ev_end, h->hs[2]), "pipeline event");
     PW_CUDA(cudaStreamWaitEvent(us, h->ev_end, 0), "pipeline wait");
-    PW_CUDA(cudaStreamSynchronize(h->hs[2]), "pw_tendencies_host synchronize");
+    if (wait) PW_CUDA(cudaStreamSynchronize(h->hs[2]), "pw_tendencies_host synchronize");
     return PW_OK;
+}
+
+pw_status_t pw_tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
+                               void* sw, const float* scale, pw_stream_t stream) {
+    return tendencies_host(h, u, v, w, su, sv, sw, scale, stream, true);
+}
+
+pw_status_t pw_tendencies_host_async(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
+                                     void* sw, const float* scale, pw_stream_t stream) {
+    return tendencies_host(h, u, v, w, su, sv, sw, scale, stream, false);
 }
 
 // Storage scales of a step call: the state is read and written with the same

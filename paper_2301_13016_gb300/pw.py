@@ -59,6 +59,7 @@ SIGNATURES = [
     ("pw_get_adjoint_config", ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     ("pw_tendencies", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_tendencies_host", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
+    ("pw_tendencies_host_async", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _FP, _VP]),
     ("pw_fill_halo_periodic", ctypes.c_int, [_VP, _VP, _VP]),
     ("pw_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _VP]),
     ("pw_step", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _I32, _FP, _VP]),
@@ -292,6 +293,19 @@ class PW:
         _check(lib().pw_tendencies_host(self.h, _ptr(u, g, "u", **H), _ptr(v, g, "v", **H), _ptr(w, g, "w", **H),
                                         _ptr(su, g, "su", **H), _ptr(sv, g, "sv", **H), _ptr(sw, g, "sw", **H),
                                         sp[0] if sp else None, _stream_ptr(stream)), "pw_tendencies_host")
+
+    def tendencies_host_async(self, u, v, w, su, sv, sw, scale=None, stream=None):
+        """HOST tensors in and out, returns once enqueued: the outputs are
+        ready after sync(stream); keep the tensors alive and unchanged until
+        then (pinned memory for overlap)."""
+        g = self.grid
+        sp = _scale_arg(scale)
+        H = dict(host=True)
+        _check(lib().pw_tendencies_host_async(self.h, _ptr(u, g, "u", **H), _ptr(v, g, "v", **H),
+                                              _ptr(w, g, "w", **H), _ptr(su, g, "su", **H), _ptr(sv, g, "sv", **H),
+                                              _ptr(sw, g, "sw", **H), sp[0] if sp else None, _stream_ptr(stream)),
+               "pw_tendencies_host_async")
+        self._keep = (u, v, w, su, sv, sw, sp)   # alive until the next call
 
     def step(self, u, v, w, tmp_u, tmp_v, tmp_w, dt, nsteps, scale=None, stream=None):
         """nsteps forward-Euler steps in place on (u, v, w); tmp_* are scratch."""

@@ -294,6 +294,31 @@ def test_host_path_matches_device_path(shape, layout):
         assert torch.all(t[~inside] == 7.0)
 
 
+@pytest.mark.parametrize("shape", [(256, 20, 64), (36, 8, 5)], ids=["pipelined", "unpipelined"])
+def test_host_path_async_calls_back_to_back(shape):
+    """Three asynchronous host calls on one handle without waiting, with
+    different inputs and outputs, then one sync: each output equals the
+    device path's result for its own inputs (the calls share the staging
+    buffers; the next call's inputs travel while the last call's outputs come
+    back)."""
+    nx, ny, nz = shape
+    c, f, g, h, dev, outs = setup(nx, ny, nz)
+    sets = []
+    for seed in (11, 12, 13):
+        d = [g.from_dense(x) for x in inputs.random_fields(nx, ny, nz, seeds=(seed, seed + 10, seed + 20))]
+        o = [g.alloc(fill=NAN) for _ in range(3)]
+        run(h, d, o)
+        hin = [t.cpu().pin_memory() for t in d]
+        hout = [torch.full((g.alloc_elems,), 7.0, dtype=torch.float32).pin_memory() for _ in range(3)]
+        sets.append((dense_out(g, o), hin, hout))
+    for _, hin, hout in sets:
+        h.tendencies_host_async(*hin, *hout)
+    h.sync()
+    for ref, hin, hout in sets:
+        for x, t in zip(ref, hout):
+            assert np.array_equal(interior(x), interior(g.to_dense(t).numpy()))
+
+
 def test_binding_rejects_tensors_on_the_wrong_side():
     """Host tensors never reach a device entry point (the GPU would fault on
     the address) and device tensors never reach the host entry point."""
