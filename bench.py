@@ -659,9 +659,7 @@ def form_batch(args):
         cfg, times = dict(lanes_x=lx, ty=ty, stages=st, ctas_per_sm=cps), {}
         b.set_config(**cfg)
     else:
-        cfg, times = autotune.tune_batch(b, flds, reps=3, force=True,
-                                         cache_path=os.path.join(ROOT, "gpurun_out", "tune_batch.json")
-                                         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        cfg, times = autotune.tune_batch(b, flds, reps=3, force=True)
     tune_s = time.perf_counter() - t0
     f = lambda: b.tendencies(*flds, stream=stream)
     for _ in range(args.warmup):
