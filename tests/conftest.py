@@ -14,6 +14,6 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # A gpu-marked test is never silently skipped on a GPU machine; on a CPU-only
+    # A gpu-marked test is never silently skipped on a machine with a GPU; on a CPU-only
     # machine the marker expression (-m "not gpu") deselects it.
     pass
