@@ -41,7 +41,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.m
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
                   for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
 FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16", "precision",
-         "batch", "adjoint", "latency64", "hostlink"]
+         "batch", "batch-bf16", "adjoint", "latency64", "hostlink"]
 
 
 def parse():
@@ -634,7 +634,7 @@ def form_precision(args):
                {"errors": out})
 
 
-def form_batch(args):
+def form_batch(args, dtype="f32"):
     import paper_2301_13016_gb300 as pwlib
     from paper_2301_13016_gb300 import autotune, inputs
     stream = torch.cuda.current_stream()
@@ -642,7 +642,7 @@ def form_batch(args):
     shapes = inputs.batch_shapes(n=args.batch_grids)
     grids, coeffs, dev, outs = [], [], [], []
     for q, (nx, ny, nz) in enumerate(shapes):
-        g = pwlib.Grid(nx, ny, nz)
+        g = pwlib.Grid(nx, ny, nz, dtype=dtype)
         c = inputs.make_coeffs(nz)
         d = inputs.random_fields(nx, ny, nz, device="cuda", seeds=(10 + 3 * q, 11 + 3 * q, 12 + 3 * q))
         grids.append(g)
@@ -669,16 +669,18 @@ def form_batch(args):
     info = b.info()
     val = info["cells"] / (ms / 1e3) / 1e9
     peak, kind = measured_peak()
-    achieved = 24 * info["cells"] / (ms / 1e3) / 1e9
+    bpc = 24 if dtype == "f32" else 12
+    achieved = bpc * info["cells"] / (ms / 1e3) / 1e9
     n = args.batch_grids
-    _form_line(args, "batch", f"PW tendencies Gcell/s, {n} independent grids in one persistent graph-replayed launch",
+    name = "batch" if dtype == "f32" else f"batch-{dtype}"
+    _form_line(args, name, f"PW tendencies Gcell/s, {n} independent grids in one persistent graph-replayed launch",
                val, "Gcell/s", {"workload": f"{n} grids, nx, ny ~ U{{32..384 step 4}}, nz ~ U{{32..128}} (seed 2304), "
-                                            "FP32, random 10*N(0,1)", "cells": info["cells"],
-                                "items": info["items"], "ctas": info["ctas"], "tile": cfg},
-               {"dtype": "f32", "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
+                                            f"{dtype.upper()} storage, FP32 math, random 10*N(0,1)",
+                                "cells": info["cells"], "items": info["items"], "ctas": info["ctas"], "tile": cfg},
+               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
                 "autotune_s": tune_s, "autotune_ms": times,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": 24},
+                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": bpc},
                 "gpu_launches": args.steps})
 
 
@@ -973,6 +975,7 @@ def main():
              "step2": lambda: form_step(args, "f32", 2), "step2-bf16": lambda: form_step(args, "bf16", 2),
              "step2-f16": lambda: form_step(args, "f16", 2),
              "precision": lambda: form_precision(args), "batch": lambda: form_batch(args),
+             "batch-bf16": lambda: form_batch(args, "bf16"),
              "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args),
              "hostlink": lambda: form_hostlink(args)}[args.form]()
     finally:
