@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-grids", type=int, default=512, help="batch form: number of grids")
-    p.add_argument("--batch-tile", default="", help="batch form: LANES,TY,STAGES,CTAS_PER_SM (skips the autotuner)")
+    p.add_argument("--batch-tile", default="", help="batch form: LANES,TY,STAGES,CTAS_PER_SM[,ROWS] (skips the autotuner)")
     p.add_argument("--skip-fp32-ref", action="store_true",
                    help="forms: do not time the FP32 tendency form beside them (small profiling runs)")
     p.add_argument("--form", choices=FORMS, default="tend",
@@ -655,8 +655,8 @@ def form_batch(args, dtype="f32"):
             [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
     t0 = time.perf_counter()
     if args.batch_tile:
-        lx, ty, st, cps = (int(x) for x in args.batch_tile.split(","))
-        cfg, times = dict(lanes_x=lx, ty=ty, stages=st, ctas_per_sm=cps), {}
+        v = [int(x) for x in args.batch_tile.split(",")]
+        cfg, times = dict(lanes_x=v[0], ty=v[1], stages=v[2], ctas_per_sm=v[3], rows=v[4] if len(v) > 4 else 0), {}
         b.set_config(**cfg)
     else:
         cfg, times = autotune.tune_batch(b, flds, reps=3, force=True)

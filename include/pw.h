@@ -377,13 +377,16 @@ typedef struct pw_batch_s *pw_batch_t;
 pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t *coeffs,
                             pw_batch_t *out);
 
-/* Tile shape of the batched kernel: lanes_x (32 or 16), ty, stages from the
- * instantiated set (32,4,4) (32,8,4) (16,4,4) (16,8,4); ctas_per_sm = resident
- * CTAs per SM of the persistent launch (0 = as many as fit).  Rebuilds the
- * work list; the next call captures a new graph.  The autotuner
- * (paper_2301_13016_gb300.autotune) chooses these by measurement. */
+/* Tile shape of the batched kernel: lanes_x (32 or 16), ty, stages,
+ * rows_per_thread (1, or 2: a cell and the one a row further on in packed
+ * FP32x2 arithmetic, 16-bit storage only; the same bits) from the
+ * instantiated set (32,4,4,1) (32,8,4,1) (16,4,4,1) (16,8,4,1) (32,8,4,2)
+ * (16,8,4,2), zero fields at (32, 4, 4, 1); others give PW_ERR_UNSUPPORTED.
+ * ctas_per_sm = resident CTAs per SM of the persistent launch (0 = as many as
+ * fit).  Rebuilds the work list; the next call captures a new graph.  The
+ * autotuner (paper_2301_13016_gb300.autotune) chooses these by measurement. */
 pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages,
-                                int32_t ctas_per_sm);
+                                int32_t ctas_per_sm, int32_t rows_per_thread);
 
 /* Work items, interior cells and persistent CTAs of the current shape (any
  * output pointer may be NULL). */

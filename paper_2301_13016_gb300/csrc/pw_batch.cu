@@ -35,23 +35,24 @@ struct BatchGridDev {
 #ifndef PW_BATCH_MINB
 #define PW_BATCH_MINB 0
 #endif
-template <typename T, int LX, int TY, int S>
+template <typename T, int LX, int TY, int S, int RP>
 constexpr int batch_min_blocks() {
-    using L = TmaLayout<T, LX, TY, S>;
+    using L = TmaLayout<T, LX, TY, S, 4, RP>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
     constexpr int m = by_smem < by_threads ? by_smem : by_threads;
-    constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S>();
+    constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S, 4, RP>();
     return want < m ? want : m;
 }
 
-template <typename T, int LX, int TY, int S>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (batch_min_blocks<T, LX, TY, S>()))
+// RP = 2: two rows per thread in packed FP32x2 arithmetic (16-bit storage).
+template <typename T, int LX, int TY, int S, int RP>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, 4, RP>::THREADS, (batch_min_blocks<T, LX, TY, S, RP>()))
     tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                      const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
                      int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MarchSmem<T, LX, TY, S> sm(smem_raw);
+    MarchSmem<T, LX, TY, S, 4, RP> sm(smem_raw);
     const int tid = threadIdx.y * 32 + threadIdx.x;
     sm.init(tid);
     uint32_t ring = 0;
@@ -72,34 +73,40 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S>::THREADS, (batch_min_b
         const int ke = (int)(((long long)(seg + 1) * nz) / bg.nseg);
         const CoefDev cf{bg.tcx, bg.tcy, bg.tz};
         const CUtensorMap* m = maps + 3 * (size_t)item.x;
-        if (!march_tile<T, LX, TY, S, MODE_TEND>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1], (T*)bg.o[2],
+        if (!march_tile<T, LX, TY, S, MODE_TEND, 4, RP>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1], (T*)bg.o[2],
                                                  bg.g, bg.ox, fold_coef(cf, sc), 0.f, bx, by, kb, ke, ring, err))
             break;
     }
 }
 
-#define PW_BATCH_CONFIGS(X) X(32, 4, 4) X(32, 8, 4) X(16, 4, 4) X(16, 8, 4)
+// Instantiated tile shapes (lanes per row, rows, stages, rows per thread);
+// two rows per thread for 16-bit storage only.
+#define PW_BATCH_CONFIGS(X) X(32, 4, 4, 1) X(32, 8, 4, 1) X(16, 4, 4, 1) X(16, 8, 4, 1) X(32, 8, 4, 2) X(16, 8, 4, 2)
 
-template <typename T, int LX, int TY, int S>
+template <typename T, int LX, int TY, int S, int RP>
 static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,
                               const int2* items, int n_items, int* counter, const Scales& sc, int* err, int ctas,
                               cudaStream_t s) {
-    using L = TmaLayout<T, LX, TY, S>;
-    auto kern = tma_batch_kernel<T, LX, TY, S>;
+  if constexpr (!nc_ok<T, 4, RP>()) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using L = TmaLayout<T, LX, TY, S, 4, RP>;
+    auto kern = tma_batch_kernel<T, LX, TY, S, RP>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
     kern<<<ctas, dim3(32, L::WARPS), L::SMEM, s>>>(grids, maps, items, n_items, counter, sc, err);
     return cudaGetLastError();
+  }
 }
 
 template <typename T>
 static cudaError_t batch_t(const TmaConfig& c, bool query, int* bps, const BatchGridDev* grids,
                            const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
                            int* err, int ctas, cudaStream_t s) {
-#define PW_BD(LX_, TY_, S_)                                                                                \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_)                                                      \
-        return batch_inst<T, LX_, TY_, S_>(query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+#define PW_BD(LX_, TY_, S_, RP_)                                                                           \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.rp == RP_)                                       \
+        return batch_inst<T, LX_, TY_, S_, RP_>(query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
     PW_BATCH_CONFIGS(PW_BD)
 #undef PW_BD
     return cudaErrorInvalidConfiguration;
@@ -117,9 +124,10 @@ static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool query,
     return cudaErrorInvalidValue;
 }
 
-static bool batch_config_supported(const TmaConfig& c) {
-#define PW_BS(LX_, TY_, S_) \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_) return true;
+static bool batch_config_supported(const TmaConfig& c, pw_dtype_t dt) {
+    if (c.rp == 2 && dt == PW_F32) return false;
+#define PW_BS(LX_, TY_, S_, RP_) \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.rp == RP_) return true;
     PW_BATCH_CONFIGS(PW_BS)
 #undef PW_BS
     return false;
@@ -305,12 +313,16 @@ pw_status_t pw_batch_destroy(pw_batch_t b) {
     return PW_OK;
 }
 
-pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages, int32_t ctas_per_sm) {
+pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages, int32_t ctas_per_sm,
+                                int32_t rows_per_thread) {
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (rows_per_thread < 0 || rows_per_thread > 2) return bfail(PW_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
     TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
-    if (!batch_config_supported(c))
-        return internal_fail(PW_ERR_UNSUPPORTED, "no batched kernel instance for lanes_x=%d ty=%d stages=%d", c.lx,
-                             c.ty, c.stages);
+    c.rp = rows_per_thread ? rows_per_thread : 1;
+    if (!batch_config_supported(c, b->dtype))
+        return internal_fail(PW_ERR_UNSUPPORTED,
+                             "no batched kernel instance for lanes_x=%d ty=%d stages=%d rows_per_thread=%d (dtype %d)",
+                             c.lx, c.ty, c.stages, c.rp, (int)b->dtype);
     if (ctas_per_sm < 0) return bfail(PW_ERR_ARG, "ctas_per_sm must be >= 0");
     b->cfg = c;
     b->ctas_per_sm = ctas_per_sm;

@@ -72,7 +72,7 @@ SIGNATURES = [
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
     ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
                                        ctypes.POINTER(_VP)]),
-    ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     ("pw_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(_I32)]),
     ("pw_batch_tendencies", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -428,8 +428,10 @@ class Batch:
         except Exception:
             pass
 
-    def set_config(self, lanes_x=0, ty=0, stages=0, ctas_per_sm=0):
-        _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(ty), int(stages), int(ctas_per_sm)),
+    def set_config(self, lanes_x=0, ty=0, stages=0, ctas_per_sm=0, rows=0):
+        """Tile shape of the batched kernel (0 = default field); rows = rows
+        per thread (2: packed FP32x2 on row pairs, 16-bit storage)."""
+        _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(ty), int(stages), int(ctas_per_sm), int(rows)),
                "pw_batch_set_config")
 
     def info(self):

@@ -81,6 +81,30 @@ def test_batch_graph_replay_and_pointer_change():
             assert torch.allclose(x, y, rtol=0, atol=0, equal_nan=True)
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("cfg", [(32, 8, 4), (16, 8, 4)])
+def test_batch_two_rows_per_thread_equals_single_grid(dtype, cfg):
+    """16-bit batches with two rows per thread (packed FP32x2) give the bits of
+    the single-grid kernel in the same shape, grid by grid; FP32 batches
+    reject that shape."""
+    b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES, dtype=dtype)
+    lx, ty, st = cfg
+    b.set_config(lanes_x=lx, ty=ty, stages=st, rows=2)
+    _run(b, dev, outs)
+    for g, c, d, o in zip(grids, coeffs, dev, outs):
+        h = pwlib.PW(g, c)
+        h.set_tma_config(ty, st, 1, lanes_x=lx, cells=4, rows=2)
+        single = [g.alloc(fill=NAN) for _ in range(3)]
+        h.tendencies(*d, *single)
+        h.sync()
+        for x, y in zip(o, single):
+            assert torch.equal(x.view(torch.int16), y.view(torch.int16))
+    b32, *_ = _make_batch(SHAPES[:2])
+    with pytest.raises(pwlib.PwError) as e:
+        b32.set_config(lanes_x=32, ty=8, stages=4, rows=2)
+    assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
+
+
 def test_batch_many_small_grids_bf16():
     shapes = inputs.batch_shapes(n=48, nxy=(32, 160), nzr=(3, 12))
     b, grids, coeffs, fields, dev, outs = _make_batch(shapes, dtype="bf16")
