@@ -67,8 +67,9 @@ def test_adjoint_full_array_matches_oracle(shape, anelastic):
 
 @pytest.mark.parametrize("shape", [(64, 12, 8), (36, 7, 6), (260, 9, 5), (128, 16, 20)])
 @pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
-def test_adjoint_periodic_matches_folded_oracle(shape, kernel):
-    c, q, lam, g, h, dq, dl = _setup(*shape, periodic_q=True)
+@pytest.mark.parametrize("anelastic", [False, True], ids=["boussinesq", "anelastic"])
+def test_adjoint_periodic_matches_folded_oracle(shape, kernel, anelastic):
+    c, q, lam, g, h, dq, dl = _setup(*shape, anelastic=anelastic, periodic_q=True)
     out = [g.alloc(fill=NAN) for _ in range(3)]
     h.set_kernel(kernel)
     h.adjoint(*dq, *dl, *out, alpha=1.0, flags=pwlib.PW_ADJ_PERIODIC)

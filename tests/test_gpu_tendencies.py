@@ -34,6 +34,25 @@ def test_parity_random(shape, kernel):
     assert max(rel_errs(got, [r.astype(np.float64) for r in ref32])) <= TOL
 
 
+@pytest.mark.parametrize("shape", [(128, 16, 8), (388, 37, 5), (256, 24, 20)], ids=["128", "388", "256"])
+@pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
+def test_parity_anelastic_coefficients(shape, kernel):
+    """Anelastic vertical coefficients (tzc1 != tzc2, tzd1 != tzd2), where a
+    swapped or mis-indexed vertical coefficient shows; several k segments
+    on the TMA kernel."""
+    c = inputs.make_coeffs(shape[2], anelastic=True)
+    assert np.abs(c.tzc1 - c.tzc2).max() > 0 and np.abs(c.tzd1 - c.tzd2).max() > 0
+    c, f, g, h, dev, outs = setup(*shape, coeffs=c)
+    h.set_kernel(kernel)
+    for nseg in ((0, 3) if kernel == 2 else (0,)):
+        if kernel == 2:
+            h.set_tma_config(nseg=nseg)
+        run(h, dev, outs)
+        assert h.last_kernel == kernel
+        ref64 = oracle.tendencies(*[x.numpy() for x in f], c)
+        assert max(rel_errs(dense_out(g, outs), ref64)) <= TOL
+
+
 @pytest.mark.parametrize("shape", [(64, 64, 64), (388, 37, 5), (36, 12, 3)], ids=["64", "388", "36"])
 def test_parity_narrow_tiles(shape):
     c, f, g, h, dev, outs = setup(*shape)
