@@ -105,6 +105,33 @@ def test_batch_two_rows_per_thread_equals_single_grid(dtype, cfg):
     assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("rows", [1, 2])
+def test_batch_scaled_fp16_equals_single_grid_and_follows_scale_changes(rows):
+    """FP16 batches with power-of-two storage scales give the single-grid
+    kernel's bits under the same scales, and a change of scales between calls
+    takes effect (the replayed graph is captured again)."""
+    shapes = SHAPES[:4]
+    b, grids, coeffs, fields, dev, outs = _make_batch(shapes, dtype="f16")
+    b.set_config(lanes_x=16, ty=8, stages=4, rows=rows)
+    results = []
+    for sc in ([1.0] * 6, [0.5, 0.5, 0.5, 8.0, 8.0, 8.0]):
+        _run(b, dev, outs, scale=sc)
+        results.append([[t.clone() for t in o] for o in outs])
+        for g, c, d, o in zip(grids, coeffs, dev, outs):
+            h = pwlib.PW(g, c)
+            h.set_tma_config(8, 4, 1, lanes_x=16, cells=4, rows=rows)
+            single = [g.alloc(fill=NAN) for _ in range(3)]
+            h.tendencies(*d, *single, scale=sc)
+            h.sync()
+            for x, y in zip(o, single):
+                assert torch.equal(x.view(torch.int16), y.view(torch.int16))
+    # physical in-scale 1/2 and out-scale 8: stored outputs 8 * (1/4) = 2x the unscaled ones
+    for a, bb in zip(results[0], results[1]):
+        for x, y in zip(a, bb):
+            m = torch.isfinite(x) & (x.abs() < 1e4) & (x.abs() > 1e-4)   # no overflow, no subnormals
+            assert torch.equal(y[m].float(), 2 * x[m].float())
+
+
 def test_batch_many_small_grids_bf16():
     shapes = inputs.batch_shapes(n=48, nxy=(32, 160), nzr=(3, 12))
     b, grids, coeffs, fields, dev, outs = _make_batch(shapes, dtype="bf16")
