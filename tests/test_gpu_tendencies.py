@@ -53,6 +53,21 @@ def test_parity_anelastic_coefficients(shape, kernel):
         assert max(rel_errs(dense_out(g, outs), ref64)) <= TOL
 
 
+@pytest.mark.parametrize("halo", [2, 3])
+@pytest.mark.parametrize("kernel", [1, 2], ids=["generic", "tma"])
+def test_parity_deeper_halo(halo, kernel):
+    """Grids with a deeper lateral halo (room for periodic images): the scheme
+    still reads one halo cell, wherever the interior sits in the layout."""
+    nx, ny, nz = 132, 21, 9
+    g = pwlib.Grid(nx, ny, nz, halo=halo)
+    c, f, g, h, dev, outs = setup(nx, ny, nz, grid=g)
+    h.set_kernel(kernel)
+    run(h, dev, outs)
+    assert h.last_kernel == kernel
+    ref64 = oracle.tendencies(*[x.numpy() for x in f], c)
+    assert max(rel_errs(dense_out(g, outs), ref64)) <= TOL
+
+
 @pytest.mark.parametrize("shape", [(64, 64, 64), (388, 37, 5), (36, 12, 3)], ids=["64", "388", "36"])
 def test_parity_narrow_tiles(shape):
     c, f, g, h, dev, outs = setup(*shape)
