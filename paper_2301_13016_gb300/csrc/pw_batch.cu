@@ -230,6 +230,13 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t* grids, const pw_coeffs_t
     if (!b) return bfail(PW_ERR_OOM, "host allocation of the batch failed");
     b->n = n;
     b->dtype = grids[0].dtype;
+    // 16-bit storage starts with the packed two-row tile, the fastest measured
+    // on the 512-grid BF16 batch (6.7 against 8.8 ms for the one-row 32 x 4 tile)
+    if (b->dtype != PW_F32) {
+        b->cfg.lx = 16;
+        b->cfg.ty = 8;
+        b->cfg.rp = 2;
+    }
     size_t tz_total = 0;
     for (int q = 0; q < n; ++q) {
         pw_status_t s = validate_grid(&grids[q]);
