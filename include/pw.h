@@ -373,8 +373,9 @@ pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void *a, float sa, cons
 typedef struct pw_batch_s *pw_batch_t;
 
 /* Create a batch: grids[n] and coeffs[n] (HOST arrays, copied).  Allocates
- * the device tables and the work list; the tile shape starts at (32, 4, 4, 1)
- * for FP32 and at (16, 8, 4, 2) for 16-bit storage. */
+ * the device tables and the work list; the tile shape starts at (lanes, 4, 4,
+ * 1) for FP32 and (lanes, 8, 4, 2) for 16-bit storage, lanes = 16 when the
+ * cells lie mostly in grids narrower than 256 columns, else 32. */
 pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t *coeffs,
                             pw_batch_t *out);
 

@@ -230,12 +230,22 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t* grids, const pw_coeffs_t
     if (!b) return bfail(PW_ERR_OOM, "host allocation of the batch failed");
     b->n = n;
     b->dtype = grids[0].dtype;
-    // 16-bit storage starts with the packed two-row tile, the fastest measured
-    // on the 512-grid BF16 batch (6.7 against 8.8 ms for the one-row 32 x 4 tile)
-    if (b->dtype != PW_F32) {
-        b->cfg.lx = 16;
-        b->cfg.ty = 8;
-        b->cfg.rp = 2;
+    // Starting tile (the autotuner refines it): 16-lane tiles when the cells
+    // lie mostly in grids narrower than 256 columns, and for 16-bit storage
+    // the packed two-row tile of 8 rows.  On the 512-grid batch (widths
+    // 32..384): FP32 7.9 ms against 8.6 for 32 x 4; BF16 6.7 against 8.8.
+    {
+        double cells = 0.0, wx = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const double c = (double)grids[q].nx * grids[q].ny * grids[q].nz;
+            cells += c;
+            wx += c * grids[q].nx;
+        }
+        b->cfg.lx = (cells > 0.0 && wx / cells < 256.0) ? 16 : 32;
+        if (b->dtype != PW_F32) {
+            b->cfg.ty = 8;
+            b->cfg.rp = 2;
+        }
     }
     size_t tz_total = 0;
     for (int q = 0; q < n; ++q) {
