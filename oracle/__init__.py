@@ -1,7 +1,7 @@
 """CPU oracle for the Piacsek-Williams advection scheme (Sec. 2.2, Sec. 4).
 
 TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, the smoke check and the
-benchmark's CPU-baseline leg import this package.  It shares no code with the
+benchmark's CPU-baseline leg and reference arm import this package.  It shares no code with the
 CUDA library (paper_2301_13016_gb300) and imports nothing from it.
 
 Thin ctypes wrapper over oracle/pw_oracle.c (plain C loop nests, FP64 and FP32).
