@@ -18,7 +18,8 @@ def _make_batch(shapes, dtype="f32", seed0=10):
     grids, coeffs, fields, dev = [], [], [], []
     for q, (nx, ny, nz) in enumerate(shapes):
         g = pwlib.Grid(nx, ny, nz, dtype=dtype)
-        c = inputs.make_coeffs(nz, dx=100.0 + q, dy=90.0 + q)
+        # every other grid with the anelastic coefficient set (tzc1 != tzc2)
+        c = inputs.make_coeffs(nz, dx=100.0 + q, dy=90.0 + q, anelastic=(q % 2 == 1))
         f = inputs.random_fields(nx, ny, nz, seeds=(seed0 + 3 * q, seed0 + 3 * q + 1, seed0 + 3 * q + 2))
         grids.append(g)
         coeffs.append(c)
