@@ -40,7 +40,7 @@ FLOPS_PER_CELL = 63              # 21 useful FLOPs per field (Sec. 4 op structur
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
                   for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
-FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16", "precision",
+FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16",
          "batch", "batch-bf16", "adjoint", "latency64", "hostlink"]
 
 
@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-grids", type=int, default=512, help="batch form: number of grids")
-    p.add_argument("--batch-tile", default="", help="batch form: LANES,TY,STAGES,CTAS_PER_SM[,ROWS] (skips the autotuner)")
+    p.add_argument("--batch-tile", default="", help="batch form: LANES,TY,STAGES,CTAS_PER_SM[,ROWS[,CELLS]] (skips the autotuner)")
     p.add_argument("--skip-fp32-ref", action="store_true",
                    help="forms: do not time the FP32 tendency form beside them (small profiling runs)")
     p.add_argument("--form", choices=FORMS, default="tend",
@@ -129,6 +129,42 @@ def kernel_source_hash():
         text = re.sub(r"//[^\n]*", " ", text)
         h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def source_version():
+    """Which code produced this line: the git commit when the checkout has its
+    .git directory (read from the files, no git process), and always the
+    sha256[:16] of the product sources (package, header, oracle, this file),
+    which a checkout of any commit reproduces with the same function."""
+    git_sha = None
+    try:
+        head = open(os.path.join(ROOT, ".git", "HEAD")).read().strip()
+        if head.startswith("ref: "):
+            ref = head[5:]
+            path = os.path.join(ROOT, ".git", ref)
+            if os.path.exists(path):
+                git_sha = open(path).read().strip()
+            else:
+                for ln in open(os.path.join(ROOT, ".git", "packed-refs")):
+                    if ln.strip().endswith(" " + ref):
+                        git_sha = ln.split()[0]
+        else:
+            git_sha = head
+    except OSError:
+        pass
+    files = []
+    for sub, exts in (("paper_2301_13016_gb300", (".py", ".cu", ".cuh", ".h")), ("include", (".h",)),
+                      ("oracle", (".c", ".h", ".py"))):
+        for dirpath, dirnames, names in os.walk(os.path.join(ROOT, sub)):
+            dirnames[:] = sorted(d for d in dirnames if not d.startswith(("_", ".")))
+            files += [os.path.join(dirpath, n) for n in names if n.endswith(exts)]
+    files += [os.path.join(ROOT, "bench.py"), os.path.join(ROOT, "__graft_entry__.py")]
+    h = hashlib.sha256()
+    for path in sorted(files):
+        h.update(os.path.relpath(path, ROOT).encode() + b"\0")
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return {"git_sha": git_sha, "source_sha256": h.hexdigest()[:16]}
 
 
 def profiled_traffic():
@@ -299,7 +335,8 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": {"workload": workload_label(w), "nx": w["nx"], "ny": w["ny"],
                                             "nz": w["nz"], "sample_ny": ny},
             "cpu_baseline": {"value": val, "unit": "Gcell/s", "cores": n, "kind": "oracle", "sample": sample},
-            "e2e": {"value": val, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": val, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "version": source_version()}
     print(json.dumps(line), flush=True)
 
 
@@ -438,6 +475,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": args.steps,
         "clocks": clocks,
         "bf16_storage": bf16,
+        "version": source_version(),
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, slab=slab)
@@ -485,6 +523,7 @@ def _form_line(args, form, metric, value, unit, config, extra):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic", "config": config}
     line.update(extra)
+    line["version"] = source_version()
     print(json.dumps(line), flush=True)
 
 
@@ -582,58 +621,6 @@ def form_step(args, dtype, spp=1):
                extra)
 
 
-def form_precision(args):
-    """100 fused Euler steps, dt = 1 s, on a smooth field with w = 0 initially
-    and on the random field until divergence: max|err|/max|ref| per field
-    against the FP64 oracle's rollout every 10 steps, FP32 / BF16 / FP16 state."""
-    import numpy as np
-    import oracle
-    import paper_2301_13016_gb300 as pwlib
-    from paper_2301_13016_gb300 import inputs, precision
-    nx = ny = 256
-    nz = 64
-    nsteps, every = 100, 10
-    c = inputs.make_coeffs(nz)
-    out = {}
-    for field in ("smooth_w0", "random"):
-        dense = (inputs.smooth_fields(nx, ny, nz, w_zero=True) if field == "smooth_w0"
-                 else inputs.random_fields(nx, ny, nz))
-        ref = [x.numpy().astype(np.float64) for x in dense]
-        refs = []
-        for n in range(0, nsteps, every):
-            ref = list(oracle.step(*ref, c, 1.0, every))
-            refs.append(ref)
-        res = {}
-        for dtype, spp in (("f32", 1), ("bf16", 1), ("f16", 1), ("bf16", 2), ("f16", 2)):
-            g = pwlib.Grid(nx, ny, nz, dtype=dtype, halo=spp)
-            h = pwlib.PW(g, c)
-            h.set_step_blocking(spp)
-            sc = precision.suggest_scales([max(float(x.abs().max()), 1.0) for x in dense], c, dtype)[:3]
-            q = [g.from_dense(x, scale=s) for x, s in zip(dense, sc)]
-            tmp = [g.alloc() for _ in range(3)]
-            errs = []
-            for n in range(nsteps // every):
-                h.step(*q, *tmp, 1.0, every, scale=sc)
-                h.sync()
-                got = [g.to_dense(t, s).numpy() for t, s in zip(q, sc)]
-                r = refs[n]
-                umax = np.abs(r[0][1:-1, 1:-1, 1:-1]).max()
-                row = {"step": (n + 1) * every, "max_ref": float(umax)}
-                for name, a, b in zip("uvw", got, r):
-                    d = np.abs(a[1:-1, 1:-1, 1:-1] - b[1:-1, 1:-1, 1:-1])
-                    den = max(np.abs(b[1:-1, 1:-1, 1:-1]).max(), umax if name == "w" else 0.0)
-                    row[name] = float(d.max() / den) if np.isfinite(d).all() and den > 0 else None
-                errs.append(row)
-                if not np.isfinite(umax) or umax > 1e3 * 10:
-                    break
-            res[dtype if spp == 1 else f"{dtype}-2step"] = errs
-        out[field] = res
-    _form_line(args, "precision", "max|err|/max|ref| vs FP64 oracle per 10 steps, 100 fused Euler steps", None,
-               "relative error", {"workload": f"{nx}x{ny}x{nz}, dt = 1 s; smooth field with w = 0 initially, and "
-                                              "the random 10*N(0,1) field (diverges: errors reported until then)"},
-               {"errors": out})
-
-
 def form_batch(args, dtype="f32"):
     import paper_2301_13016_gb300 as pwlib
     from paper_2301_13016_gb300 import autotune, inputs
@@ -656,7 +643,8 @@ def form_batch(args, dtype="f32"):
     t0 = time.perf_counter()
     if args.batch_tile:
         v = [int(x) for x in args.batch_tile.split(",")]
-        cfg, times = dict(lanes_x=v[0], ty=v[1], stages=v[2], ctas_per_sm=v[3], rows=v[4] if len(v) > 4 else 0), {}
+        cfg, times = dict(lanes_x=v[0], ty=v[1], stages=v[2], ctas_per_sm=v[3], rows=v[4] if len(v) > 4 else 0,
+                          cells=v[5] if len(v) > 5 else 0), {}
         b.set_config(**cfg)
     else:
         cfg, times = autotune.tune_batch(b, flds, reps=3, force=True)
@@ -974,7 +962,7 @@ def main():
              "step": lambda: form_step(args, "f32"), "step-bf16": lambda: form_step(args, "bf16"),
              "step2": lambda: form_step(args, "f32", 2), "step2-bf16": lambda: form_step(args, "bf16", 2),
              "step2-f16": lambda: form_step(args, "f16", 2),
-             "precision": lambda: form_precision(args), "batch": lambda: form_batch(args),
+             "batch": lambda: form_batch(args),
              "batch-bf16": lambda: form_batch(args, "bf16"),
              "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args),
              "hostlink": lambda: form_hostlink(args)}[args.form]()

@@ -105,13 +105,23 @@ pw_status_t pw_grid_default(int32_t nx, int32_t ny, int32_t nz, int32_t halo, pw
                             pw_grid_t *out, int64_t *alloc_elems);
 
 /*
- * Create a handle for one grid and coefficient set on the current device.
- * Validates the layout, copies the coefficients to device memory, allocates
- * the handle's status word.  *out is NULL on failure.
+ * Create a handle for one grid and coefficient set on the current device:
+ * the grid of the three wind fields U, V, W and the coefficients of the PW
+ * scheme's source terms (Sec. 2.2: the scheme runs every model timestep on
+ * the same grid, so the handle is made once and used for every call).
+ * Validates the layout, copies the coefficients (horizontal scalars tcx,
+ * tcy and the per-level vertical arrays) to device memory, allocates the
+ * handle's status word; the caller may free its coefficient arrays on
+ * return.  Fails with PW_ERR_ARG for a bad layout or NULL argument and
+ * PW_ERR_CUDA/PW_ERR_OOM for a failed device call.  *out is NULL on failure.
  */
 pw_status_t pw_create(const pw_grid_t *grid, const pw_coeffs_t *coeffs, pw_handle_t *out);
 
-/* Release the handle and everything it allocated.  NULL is accepted. */
+/* Release the handle and everything it allocated (device memory, streams,
+ * events); the caller's field buffers are not touched.  Resource handling
+ * of this library: the paper has no counterpart.  Waits for nothing: work
+ * still queued on the handle must be finished first (pw_sync).  NULL is
+ * accepted. */
 pw_status_t pw_destroy(pw_handle_t h);
 
 /* Kernel selection for pw_tendencies, pw_step, pw_step_to and the periodic
@@ -204,10 +214,13 @@ pw_status_t pw_tendencies_host(pw_handle_t h, const void *u, const void *v, cons
  * in host memory once `stream` reaches the point after the call (it waits for
  * the call's last copy), for example after pw_sync(h, stream).  Until then
  * the host inputs must stay unchanged and the host outputs untouched.  Calls
- * on one handle may follow each other without waiting: a call's inputs travel
- * while the previous call's outputs come back (with pinned host memory; with
- * pageable memory the copies are synchronous).  Same arguments and results
- * as pw_tendencies_host.
+ * on one handle may follow each other without waiting, on one stream or on
+ * several: they share the handle's device buffers, so each call is ordered
+ * after the previous one on the GPU.  On the pipelined path (the TMA layout,
+ * nz >= 8) a call's inputs travel while the previous call's outputs come back
+ * (with pinned host memory; with pageable memory the copies are synchronous);
+ * otherwise a call starts once the previous call has finished.  Same
+ * arguments and results as pw_tendencies_host.
  */
 pw_status_t pw_tendencies_host_async(pw_handle_t h, const void *u, const void *v, const void *w,
                                      void *su, void *sv, void *sw, const float *scale, pw_stream_t stream);
@@ -379,15 +392,20 @@ typedef struct pw_batch_s *pw_batch_t;
 pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t *coeffs,
                             pw_batch_t *out);
 
-/* Tile shape of the batched kernel: lanes_x (32 or 16), ty, stages,
- * rows_per_thread (1, or 2: a cell and the one a row further on in packed
- * FP32x2 arithmetic, 16-bit storage only; the same bits) from the
- * instantiated set (32,4,4,1) (32,8,4,1) (16,4,4,1) (16,8,4,1) (32,8,4,2)
- * (16,8,4,2), zero fields at (32, 4, 4, 1); others give PW_ERR_UNSUPPORTED.
- * ctas_per_sm = resident CTAs per SM of the persistent launch (0 = as many as
- * fit).  Rebuilds the work list; the next call captures a new graph.  The
- * autotuner (paper_2301_13016_gb300.autotune) chooses these by measurement. */
-pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages,
+/* Tile shape of the batched kernel: lanes_x (32 or 16), cells (per thread
+ * along x: 4, or 8), ty, stages, rows_per_thread (1; 2: a cell and the one a
+ * row further on in packed FP32x2 arithmetic; 3: one row whose cells are
+ * packed as FP32x2 pairs along x; 2 and 3 for 16-bit storage only; all give
+ * the same bits) from the instantiated set (lanes_x, ty, stages, cells,
+ * rows_per_thread) (32,4,4,4,1) (32,8,4,4,1) (16,4,4,4,1) (16,8,4,4,1)
+ * (32,8,4,4,2) (16,8,4,4,2) (32,4,4,4,3) (32,8,4,4,3) (16,4,4,4,3)
+ * (16,8,4,4,3) (16,4,4,8,3) (16,8,4,8,3), zero fields at (32, 4, 4, 4, 1);
+ * others, and cells = 8 with a grid whose nx is not a multiple of 8, give
+ * PW_ERR_UNSUPPORTED.  ctas_per_sm = resident CTAs per SM of the persistent
+ * launch (0 = as many as fit).  Rebuilds the work list; the next call
+ * captures a new graph.  The autotuner (paper_2301_13016_gb300.autotune)
+ * chooses these by measurement. */
+pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
                                 int32_t ctas_per_sm, int32_t rows_per_thread);
 
 /* Work items, interior cells and persistent CTAs of the current shape (any
@@ -415,7 +433,9 @@ pw_status_t pw_batch_sync(pw_batch_t b, pw_stream_t stream);
 pw_status_t pw_batch_destroy(pw_batch_t b);
 
 /* Wait for `stream`, then report (and clear) any bounded-wait timeout a
- * kernel of this handle recorded, and any pending CUDA error. */
+ * kernel of this handle recorded (PW_ERR_DEVICE_TIMEOUT), and any pending
+ * CUDA error (PW_ERR_CUDA).  Error reporting of this library: the paper has
+ * no counterpart. */
 pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream);
 
 /*

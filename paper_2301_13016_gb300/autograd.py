@@ -68,7 +68,10 @@ class PWRollout(torch.autograd.Function):
         for x in (gu, gv, gw):
             g.append(torch.where(mask, x.to(torch.float32), 0.0) if x is not None
                      else torch.zeros(grid.alloc_elems, dtype=torch.float32, device=dev))
-        g2 = [torch.empty_like(t) for t in g]   # the adjoint writes every interior cell
+        # the adjoint writes every interior cell; the halo starts (and, as the
+        # periodic adjoint leaves it, stays) at zero, so the next call's
+        # incoming sensitivities have no stale values anywhere
+        g2 = [torch.zeros_like(t) for t in g]
         for s in range(len(ckpts) - 1, -1, -1):
             n0 = s * every
             m = min(every, nsteps - n0)

@@ -416,68 +416,65 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
                         LW0p[x] = keep(lw0, LW0p[x]);
                     }
                 }
+                // Each output's terms are grouped by their coefficient, so a
+                // coefficient multiplies a group's sum once instead of every
+                // term; products that two neighbouring cells share are formed
+                // once for the row: index x of the X arrays, cell o = c + 1
+                // uses x = o - 1 and o.
+                float D[NA + 1], Q[NA + 1], F[NA + 1], G[NA + 1], R[NA + 1];
+#pragma unroll
+                for (int x = 0; x <= NA; ++x) {
+                    D[x] = fmaf(LU0p[x], U0z[x], -LU0z[x] * U0p[x]);   // sv's y-pair terms, as seen from v
+                    Q[x] = U0z[x] + U0p[x];                            // u(j) + u(j+1)
+                    F[x] = LUpz[x] * U0z[x];                           // su's upper term at k+1, as seen from w
+                    G[x] = LU0z[x] * Upz[x];                           // su's upper term at k, as seen from w
+                    R[x] = U0z[x] + Upz[x];                            // u(k) + u(k+1)
+                }
 #pragma unroll
                 for (int c = 0; c < NA; ++c) {
                     const int o = c + 1;   // the cell in the X arrays; o-1 and o+1 its x neighbours
-                    float a = 0.f, b = 0.f;
-                    // ---- gu
-                    a += tcx * LU0z[o + 1] * (U0z[o + 1] + 2.f * U0z[o]);
-                    b += tcx * LU0z[o] * U0z[o - 1];
-                    a -= tcx * LU0z[o - 1] * (U0z[o - 1] + 2.f * U0z[o]);
-                    b -= tcx * LU0z[o] * U0z[o + 1];
-                    a += tcy * LU0p[o] * (V0z[o] + V0z[o + 1]);
-                    b -= tcy * LU0m[o] * (V0m[o] + V0m[o + 1]);
-                    a += keep(pu, c1p * LUpz[o] * (W0z[o] + W0z[o + 1]));
-                    b -= keep(mu, c2m * LUmz[o] * (Wmz[o] + Wmz[o + 1]));
-                    a += tcx * LV0z[o + 1] * V0z[o];
-                    b += tcx * LV0m[o + 1] * V0m[o];
-                    a -= tcx * LV0z[o] * V0z[o + 1];
-                    b -= tcx * LV0m[o] * V0m[o + 1];
-                    a += tcx * LW0z[o + 1] * W0z[o];
-                    b -= tcx * LW0z[o] * W0z[o + 1];
-                    a += keep(mw, tcx * LWmz[o + 1] * Wmz[o]);
-                    b -= keep(mw, tcx * LWmz[o] * Wmz[o + 1]);
-                    ru[c] = a + b;
-                    // ---- gv
-                    a = 0.f;
-                    b = 0.f;
-                    a += tcy * LU0p[o] * U0z[o];
-                    b += tcy * LU0p[o - 1] * U0z[o - 1];
-                    a -= tcy * LU0z[o] * U0p[o];
-                    b -= tcy * LU0z[o - 1] * U0p[o - 1];
-                    a += tcx * LV0z[o + 1] * (U0z[o] + U0p[o]);
-                    b -= tcx * LV0z[o - 1] * (U0z[o - 1] + U0p[o - 1]);
-                    a += tcy * LV0p[o] * (V0p[o] + 2.f * V0z[o]);
-                    b += tcy * LV0z[o] * V0m[o];
-                    a -= tcy * LV0m[o] * (V0m[o] + 2.f * V0z[o]);
-                    b -= tcy * LV0z[o] * V0p[o];
-                    a += keep(pu, c1p * LVpz[o] * (W0z[o] + W0p[o]));
-                    b -= keep(mu, c2m * LVmz[o] * (Wmz[o] + Wmp[o]));
-                    a += tcy * LW0p[o] * W0z[o];
-                    b -= tcy * LW0z[o] * W0p[o];
-                    a += keep(mw, tcy * LWmp[o] * Wmz[o]);
-                    b -= keep(mw, tcy * LWmz[o] * Wmp[o]);
-                    rv[c] = a + b;
-                    // ---- gw
-                    a = 0.f;
-                    b = 0.f;
-                    a += keep(pu, c1p * LUpz[o] * U0z[o]);
-                    b += keep(pu, c1p * LUpz[o - 1] * U0z[o - 1]);
-                    a += keep(pu, c1p * LVpz[o] * V0z[o]);
-                    b += keep(pu, c1p * LVpm[o] * V0m[o]);
-                    a -= keep(has_p, c2 * LU0z[o] * Upz[o]);
-                    b -= keep(has_p, c2 * LU0z[o - 1] * Upz[o - 1]);
-                    a -= keep(has_p, c2 * LV0z[o] * Vpz[o]);
-                    b -= keep(has_p, c2 * LV0m[o] * Vpm[o]);
-                    a += keep(has_p, tcx * LW0z[o + 1] * (U0z[o] + Upz[o]));
-                    b -= keep(has_p, tcx * LW0z[o - 1] * (U0z[o - 1] + Upz[o - 1]));
-                    a += keep(has_p, tcy * LW0p[o] * (V0z[o] + Vpz[o]));
-                    b -= keep(has_p, tcy * LW0m[o] * (V0m[o] + Vpm[o]));
-                    a += keep(pw, d1p * LWpz[o] * (Wpz[o] + 2.f * W0z[o]));
-                    b -= keep(has_p, d2 * LW0z[o] * Wpz[o]);
-                    a += keep(has_m, d1 * LW0z[o] * Wmz[o]);
-                    b -= keep(mw, d2m * LWmz[o] * (Wmz[o] + 2.f * W0z[o]));
-                    rw[c] = a + b;
+                    // ---- gu: u(C) in su (as a, b, d), sv and sw (as b, d)
+                    float ax = LU0z[o + 1] * fmaf(2.f, U0z[o], U0z[o + 1]);
+                    ax = fmaf(-LU0z[o - 1], fmaf(2.f, U0z[o], U0z[o - 1]), ax);
+                    ax = fmaf(LU0z[o], U0z[o - 1] - U0z[o + 1], ax);
+                    ax = fmaf(LV0z[o + 1], V0z[o], ax);
+                    ax = fmaf(-LV0z[o], V0z[o + 1], ax);
+                    ax = fmaf(LV0m[o + 1], V0m[o], ax);
+                    ax = fmaf(-LV0m[o], V0m[o + 1], ax);
+                    ax = fmaf(LW0z[o + 1], W0z[o], ax);
+                    ax = fmaf(-LW0z[o], W0z[o + 1], ax);
+                    ax += keep(mw, fmaf(LWmz[o + 1], Wmz[o], -LWmz[o] * Wmz[o + 1]));
+                    const float ay = fmaf(LU0p[o], V0z[o] + V0z[o + 1], -LU0m[o] * (V0m[o] + V0m[o + 1]));
+                    const float az = keep(pu, c1p * LUpz[o] * (W0z[o] + W0z[o + 1])) -
+                                     keep(mu, c2m * LUmz[o] * (Wmz[o] + Wmz[o + 1]));
+                    ru[c] = fmaf(tcx, ax, fmaf(tcy, ay, az));
+                    // ---- gv: v(C) in su (as b, d), sv (as a, b, d), sw (as b, d)
+                    const float bx = fmaf(LV0z[o + 1], Q[o], -LV0z[o - 1] * Q[o - 1]);
+                    float by = D[o] + D[o - 1];
+                    by = fmaf(LV0p[o], fmaf(2.f, V0z[o], V0p[o]), by);
+                    by = fmaf(-LV0m[o], fmaf(2.f, V0z[o], V0m[o]), by);
+                    by = fmaf(LV0z[o], V0m[o] - V0p[o], by);
+                    by = fmaf(LW0p[o], W0z[o], by);
+                    by = fmaf(-LW0z[o], W0p[o], by);
+                    by += keep(mw, fmaf(LWmp[o], Wmz[o], -LWmz[o] * Wmp[o]));
+                    const float bz = keep(pu, c1p * LVpz[o] * (W0z[o] + W0p[o])) -
+                                     keep(mu, c2m * LVmz[o] * (Wmz[o] + Wmp[o]));
+                    rv[c] = fmaf(tcx, bx, fmaf(tcy, by, bz));
+                    // ---- gw: w(C) in su, sv (as b, d), sw (as a, b, d)
+                    float e1 = F[o] + F[o - 1];
+                    e1 = fmaf(LVpz[o], V0z[o], e1);
+                    e1 = fmaf(LVpm[o], V0m[o], e1);
+                    float e2 = G[o] + G[o - 1];
+                    e2 = fmaf(LV0z[o], Vpz[o], e2);
+                    e2 = fmaf(LV0m[o], Vpm[o], e2);
+                    const float ex = fmaf(LW0z[o + 1], R[o], -LW0z[o - 1] * R[o - 1]);
+                    const float ey = fmaf(LW0p[o], V0z[o] + Vpz[o], -LW0m[o] * (V0m[o] + Vpm[o]));
+                    float t = keep(has_p, fmaf(tcx, ex, fmaf(tcy, ey, fmaf(-c2, e2, -d2 * LW0z[o] * Wpz[o]))));
+                    t += keep(pu, c1p * e1);
+                    t += keep(pw, d1p * LWpz[o] * fmaf(2.f, W0z[o], Wpz[o]));
+                    t += keep(has_m, d1 * LW0z[o] * Wmz[o]);
+                    t -= keep(mw, d2m * LWmz[o] * fmaf(2.f, W0z[o], Wmz[o]));
+                    rw[c] = t;
                 }
             };
             if (K >= 3 && K <= nz - 2)

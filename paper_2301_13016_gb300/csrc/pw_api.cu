@@ -96,6 +96,7 @@ struct pw_handle_s {
     static constexpr int kMaxChunks = 32;
     cudaEvent_t ev_in[kMaxChunks] = {}, ev_comp[kMaxChunks] = {}, ev_out[kMaxChunks] = {};
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+    bool host_prev_plain = false;   // the last host-path call took the one-launch path (it recorded ev_end on its stream)
     // validation scratch: 4*(nblocks+1) doubles + wk (nz+2 doubles)
     double* d_scratch = nullptr;
     int nblocks = 0;
@@ -267,6 +268,10 @@ static TmaConfig choose_tma(pw_handle_t h, bool step) {
         c.ty = u.ty ? u.ty : 4;
         c.stages = u.stages ? u.stages : 4;
         c.rp = u.rp ? u.rp : 1;
+        if (c.rp == 3) {   // one row per thread, cells paired along x
+            c.rp = 1;
+            c.xp = 1;
+        }
     } else {
         const bool half = dtype_size(gr.dtype) == 2;
         c.lx = 32;
@@ -362,6 +367,12 @@ bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms) {
     *g = h->grid;
     *num_sms = h->num_sms;
     return true;
+}
+
+int internal_handle_device(pw_handle_t h) { return h ? h->device : -1; }
+
+pw_status_t internal_check_device_ptrs(pw_handle_t h, const void* const* ps, int n) {
+    return check_device_ptrs(h, ps, n);
 }
 
 }  // namespace pw
@@ -461,15 +472,19 @@ pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int
                               int32_t nseg, int32_t rows_per_thread) {
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (nseg < 0 || nseg > h->grid.nz / 2) return fail(PW_ERR_ARG, "nseg must be in 0..nz/2");
-    if (rows_per_thread < 0 || rows_per_thread > 2) return fail(PW_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
+    if (rows_per_thread < 0 || rows_per_thread > 3)
+        return fail(PW_ERR_ARG, "rows_per_thread must be 0, 1, 2 or 3");
     TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
     c.nc = cells ? cells : 4;
     c.rp = rows_per_thread ? rows_per_thread : 1;
+    if (c.rp == 3) {
+        c.rp = 1;
+        c.xp = 1;
+    }
     if (!tma_config_supported(h->grid.dtype, c))
         return fail(PW_ERR_UNSUPPORTED,
                     "no TMA kernel instance for lanes_x=%d cells=%d ty=%d stages=%d rows_per_thread=%d (dtype %d)",
-                    c.lx, c.nc, c.ty, c.stages, c.rp, (int)h->grid.dtype);
-    if (h->grid.nx % c.nc) return fail(PW_ERR_UNSUPPORTED, "cells=%d needs nx to be a multiple of %d", c.nc, c.nc);
+                    c.lx, c.nc, c.ty, c.stages, rows_per_thread ? rows_per_thread : 1, (int)h->grid.dtype);
     h->tma_user = TmaConfig{lanes_x, ty, stages, nseg};
     h->tma_user.nc = cells;
     h->tma_user.rp = rows_per_thread;
@@ -586,7 +601,7 @@ pw_status_t pw_get_tma_config(pw_handle_t h, int32_t step, int32_t out[6]) {
     out[2] = c.ty;
     out[3] = c.stages;
     out[4] = c.nseg;
-    out[5] = c.rp;
+    out[5] = c.xp ? 3 : c.rp;
     return PW_OK;
 }
 
@@ -594,6 +609,7 @@ int32_t pw_last_kernel(pw_handle_t h) { return h ? h->last_kernel : 0; }
 
 pw_status_t pw_tendencies(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
                           void* sw, const float* scale, pw_stream_t stream) {
+    PW_RANGE("pw_tendencies");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!u || !v || !w || !su || !sv || !sw) return fail(PW_ERR_ARG, "a field pointer is NULL");
     const void* ins[3] = {u, v, w};
@@ -685,6 +701,7 @@ static cudaError_t copy_box(const pw_grid_t& g, void* dst, const void* src, int 
 // once the work is enqueued (the caller's stream waits for its last copy).
 static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, const void* w, void* su, void* sv,
                                    void* sw, const float* scale, pw_stream_t stream, bool wait) {
+    PW_RANGE(wait ? "pw_tendencies_host" : "pw_tendencies_host_async");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!u || !v || !w || !su || !sv || !sw) return fail(PW_ERR_ARG, "a field pointer is NULL");
     const pw_grid_t& g = h->grid;
@@ -715,12 +732,21 @@ static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, 
     bool ptrs_ok = true;
     for (auto p : h->d_stage) ptrs_ok = ptrs_ok && aligned16(p);
     const bool pipelined = h->kernel_kind != 1 && ptrs_ok && tma_layout_ok(g, &ox, &why) && g.nz >= 8;
+    // Every call of either path ends by recording ev_end after its last copy
+    // out.  The one-launch path runs on the caller's stream only, so it first
+    // waits for the whole of the previous call (which may have run on another
+    // stream); a pipelined call does the same after a one-launch call, and
+    // after a pipelined call relies on the per-chunk events below.
+    if (!h->ev_end) PW_CUDA(cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming), "pipeline event");
+    if (!pipelined || h->host_prev_plain) PW_CUDA(cudaStreamWaitEvent(us, h->ev_end, 0), "pipeline wait");
     if (!pipelined) {   // one copy in, one launch, one copy out
         for (int q = 0; q < 3; ++q) PW_CUDA(copy_in(q, 1, g.nz, us), "pw_tendencies_host input copy");
         pw_status_t st = pw_tendencies(h, h->d_stage[0], h->d_stage[1], h->d_stage[2], h->d_stage[3], h->d_stage[4],
                                        h->d_stage[5], scale, stream);
         if (st != PW_OK) return st;
         for (int q = 0; q < 3; ++q) PW_CUDA(copy_out(q, 1, g.nz, us), "pw_tendencies_host output copy");
+        PW_CUDA(cudaEventRecord(h->ev_end, us), "pipeline event");
+        h->host_prev_plain = true;
         if (wait) PW_CUDA(cudaStreamSynchronize(us), "pw_tendencies_host synchronize");
         return PW_OK;
     }
@@ -742,7 +768,6 @@ static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, 
         if (!h->ev_out[c]) PW_CUDA(cudaEventCreateWithFlags(&h->ev_out[c], cudaEventDisableTiming), "pipeline event");
     }
     if (!h->ev_start) PW_CUDA(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming), "pipeline event");
-    if (!h->ev_end) PW_CUDA(cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming), "pipeline event");
     const int C = std::min(pw_handle_s::kMaxChunks, std::max(2, g.nz / PW_HOST_CHUNK_LEVELS));
     Scales sc;
     bool scaled;
@@ -788,6 +813,7 @@ static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, 
     }
     h->last_kernel = 2;
     PW_CUDA(cudaEventRecord(h->ev_end, h->hs[2]), "pipeline event");
+    h->host_prev_plain = false;
     PW_CUDA(cudaStreamWaitEvent(us, h->ev_end, 0), "pipeline wait");
     if (wait) PW_CUDA(cudaStreamSynchronize(h->hs[2]), "pw_tendencies_host synchronize");
     return PW_OK;
@@ -859,6 +885,7 @@ static pw_status_t step_kernel_choice(pw_handle_t h, void* const* bufs, int n, b
 
 pw_status_t pw_step_to(pw_handle_t h, const void* u, const void* v, const void* w, void* nu, void* nv, void* nw,
                        float dt, const float* scale, pw_stream_t stream) {
+    PW_RANGE("pw_step_to");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     void* bufs[6] = {const_cast<void*>(u), const_cast<void*>(v), const_cast<void*>(w), nu, nv, nw};
     for (int a = 0; a < 6; ++a) {
@@ -881,6 +908,8 @@ pw_status_t pw_step_to(pw_handle_t h, const void* u, const void* v, const void* 
     CoefDev cf{h->tcx, h->tcy, h->d_tz};
     TmaConfig c{};
     if (use_tma) c = choose_tma(h, true);
+    if (use_tma && h->grid.nx % c.nc)
+        return fail(PW_ERR_UNSUPPORTED, "fused steps with cells=%d need nx to be a multiple of %d", c.nc, c.nc);
     st = step_pass(h, g, bufs, bufs + 3, sc, scaled, cf, dt, use_tma, ox, c, reinterpret_cast<cudaStream_t>(stream));
     if (st != PW_OK) return st;
     h->last_kernel = use_tma ? 2 : 1;
@@ -889,6 +918,7 @@ pw_status_t pw_step_to(pw_handle_t h, const void* u, const void* v, const void* 
 
 pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void* tmp_v, void* tmp_w, float dt,
                     int32_t nsteps, const float* scale, pw_stream_t stream) {
+    PW_RANGE("pw_step");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     void* bufs[6] = {u, v, w, tmp_u, tmp_v, tmp_w};
     for (int a = 0; a < 6; ++a) {
@@ -928,6 +958,8 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
     const bool use_tb2 = tb2_ok && h->steps_per_pass == 2;
     TmaConfig c{};
     if (use_tma) c = choose_tma(h, true);
+    if (use_tma && h->grid.nx % c.nc)
+        return fail(PW_ERR_UNSUPPORTED, "fused steps with cells=%d need nx to be a multiple of %d", c.nc, c.nc);
     Step2Config c2{};
     if (use_tb2 && nsteps >= 2) c2 = choose_step2(h);
     int done = 0, passes = 0, kind = use_tma ? 2 : 1;
@@ -969,6 +1001,7 @@ pw_status_t pw_step(pw_handle_t h, void* u, void* v, void* w, void* tmp_u, void*
 pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* w, const void* lsu,
                        const void* lsv, const void* lsw, void* gu, void* gv, void* gw, float alpha, int32_t flags,
                        pw_stream_t stream) {
+    PW_RANGE("pw_adjoint");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (h->grid.dtype != PW_F32) return fail(PW_ERR_UNSUPPORTED, "pw_adjoint supports FP32 fields only");
     if (!u || !v || !w || !lsu || !lsv || !lsw || !gu || !gv || !gw) return fail(PW_ERR_ARG, "a field pointer is NULL");
@@ -1025,6 +1058,7 @@ pw_status_t pw_adjoint(pw_handle_t h, const void* u, const void* v, const void* 
 }
 
 pw_status_t pw_fill_halo_periodic(pw_handle_t h, void* f, pw_stream_t stream) {
+    PW_RANGE("pw_fill_halo_periodic");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!f) return fail(PW_ERR_ARG, "field pointer is NULL");
     {
@@ -1052,6 +1086,7 @@ static pw_status_t ensure_scratch(pw_handle_t h) {
 
 pw_status_t pw_error_norms(pw_handle_t h, const void* test, float scale, const double* ref, int32_t k0, int32_t k1,
                            double* out, pw_stream_t stream) {
+    PW_RANGE("pw_error_norms");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!test || !ref || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
     if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
@@ -1072,6 +1107,7 @@ pw_status_t pw_error_norms(pw_handle_t h, const void* test, float scale, const d
 
 pw_status_t pw_weighted_dot(pw_handle_t h, const void* a, float sa, const void* b, float sb, const double* wk,
                             int32_t k0, int32_t k1, double* out, pw_stream_t stream) {
+    PW_RANGE("pw_weighted_dot");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (!a || !b || !out) return fail(PW_ERR_ARG, "a pointer is NULL");
     if (k0 < 1 || k1 > h->grid.nz || k0 > k1) return fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
@@ -1114,6 +1150,7 @@ pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream) {
 }
 
 pw_status_t pw_selftest_wait_timeout(pw_handle_t h, int64_t limit_ns, pw_stream_t stream) {
+    PW_RANGE("pw_selftest_wait_timeout");
     if (!h) return fail(PW_ERR_ARG, "handle is NULL");
     if (limit_ns < 1000000 || limit_ns > 1000000000) return fail(PW_ERR_ARG, "limit_ns must be in [1e6, 1e9]");
     cudaError_t e = launch_selftest_wait((uint64_t)limit_ns, h->d_err, reinterpret_cast<cudaStream_t>(stream));

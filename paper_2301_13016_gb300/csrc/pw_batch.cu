@@ -35,24 +35,27 @@ struct BatchGridDev {
 #ifndef PW_BATCH_MINB
 #define PW_BATCH_MINB 0
 #endif
-template <typename T, int LX, int TY, int S, int RP>
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
 constexpr int batch_min_blocks() {
-    using L = TmaLayout<T, LX, TY, S, 4, RP>;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
     constexpr int m = by_smem < by_threads ? by_smem : by_threads;
-    constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S, 4, RP>();
+    constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S, NC, RP, XP>();
     return want < m ? want : m;
 }
 
-// RP = 2: two rows per thread in packed FP32x2 arithmetic (16-bit storage).
-template <typename T, int LX, int TY, int S, int RP>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, 4, RP>::THREADS, (batch_min_blocks<T, LX, TY, S, RP>()))
+// NC cells per thread along x; RP = 2: two rows per thread in packed FP32x2
+// arithmetic; XP = 1: the cells of one row packed as FP32x2 pairs (16-bit
+// storage for both).
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
+                                  (batch_min_blocks<T, LX, TY, S, NC, RP, XP>()))
     tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                      const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
                      int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MarchSmem<T, LX, TY, S, 4, RP> sm(smem_raw);
+    MarchSmem<T, LX, TY, S, NC, RP, XP> sm(smem_raw);
     const int tid = threadIdx.y * 32 + threadIdx.x;
     sm.init(tid);
     uint32_t ring = 0;
@@ -73,25 +76,28 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, 4, RP>::THREADS, (batc
         const int ke = (int)(((long long)(seg + 1) * nz) / bg.nseg);
         const CoefDev cf{bg.tcx, bg.tcy, bg.tz};
         const CUtensorMap* m = maps + 3 * (size_t)item.x;
-        if (!march_tile<T, LX, TY, S, MODE_TEND, 4, RP>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1], (T*)bg.o[2],
-                                                 bg.g, bg.ox, fold_coef(cf, sc), 0.f, bx, by, kb, ke, ring, err))
+        if (!march_tile<T, LX, TY, S, MODE_TEND, NC, RP, XP>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1],
+                                                           (T*)bg.o[2], bg.g, bg.ox, fold_coef(cf, sc), 0.f, bx, by,
+                                                           kb, ke, ring, err))
             break;
     }
 }
 
-// Instantiated tile shapes (lanes per row, rows, stages, rows per thread);
-// two rows per thread for 16-bit storage only.
-#define PW_BATCH_CONFIGS(X) X(32, 4, 4, 1) X(32, 8, 4, 1) X(16, 4, 4, 1) X(16, 8, 4, 1) X(32, 8, 4, 2) X(16, 8, 4, 2)
+// Instantiated tile shapes (lanes per row, rows, stages, cells per thread,
+// rows per thread, x pairs); the packed forms for 16-bit storage only.
+#define PW_BATCH_CONFIGS(X) X(32, 4, 4, 4, 1, 0) X(32, 8, 4, 4, 1, 0) X(16, 4, 4, 4, 1, 0) X(16, 8, 4, 4, 1, 0) \
+    X(32, 8, 4, 4, 2, 0) X(16, 8, 4, 4, 2, 0) X(32, 4, 4, 4, 1, 1) X(32, 8, 4, 4, 1, 1) X(16, 4, 4, 4, 1, 1)      \
+    X(16, 8, 4, 4, 1, 1) X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1)
 
-template <typename T, int LX, int TY, int S, int RP>
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
 static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,
                               const int2* items, int n_items, int* counter, const Scales& sc, int* err, int ctas,
                               cudaStream_t s) {
-  if constexpr (!nc_ok<T, 4, RP>()) {
+  if constexpr (!nc_ok<T, NC, RP, XP>()) {
     return cudaErrorInvalidConfiguration;
   } else {
-    using L = TmaLayout<T, LX, TY, S, 4, RP>;
-    auto kern = tma_batch_kernel<T, LX, TY, S, RP>;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
+    auto kern = tma_batch_kernel<T, LX, TY, S, NC, RP, XP>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
@@ -104,9 +110,10 @@ template <typename T>
 static cudaError_t batch_t(const TmaConfig& c, bool query, int* bps, const BatchGridDev* grids,
                            const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
                            int* err, int ctas, cudaStream_t s) {
-#define PW_BD(LX_, TY_, S_, RP_)                                                                           \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.rp == RP_)                                       \
-        return batch_inst<T, LX_, TY_, S_, RP_>(query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+#define PW_BD(LX_, TY_, S_, NC_, RP_, XP_)                                                                     \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_)             \
+        return batch_inst<T, LX_, TY_, S_, NC_, RP_, XP_>(query, bps, grids, maps, items, n_items, counter, sc, err, \
+                                                          ctas, s);
     PW_BATCH_CONFIGS(PW_BD)
 #undef PW_BD
     return cudaErrorInvalidConfiguration;
@@ -125,9 +132,9 @@ static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool query,
 }
 
 static bool batch_config_supported(const TmaConfig& c, pw_dtype_t dt) {
-    if (c.rp == 2 && dt == PW_F32) return false;
-#define PW_BS(LX_, TY_, S_, RP_) \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.rp == RP_) return true;
+    if ((c.rp == 2 || c.xp || c.nc != 4) && dt == PW_F32) return false;
+#define PW_BS(LX_, TY_, S_, NC_, RP_, XP_) \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_) return true;
     PW_BATCH_CONFIGS(PW_BS)
 #undef PW_BS
     return false;
@@ -183,7 +190,7 @@ static void drop_graph(pw_batch_t b) {
 // the cost (a grid's ragged last column then ran with other grids' ones) and
 // 218 with y fastest.
 static pw_status_t build_items(pw_batch_t b) {
-    const int TX = 4 * b->cfg.lx, TY = b->cfg.ty;
+    const int TX = b->cfg.nc * b->cfg.lx, TY = b->cfg.ty;
     struct Item {
         int grid, tile;
         long long cost;
@@ -330,16 +337,23 @@ pw_status_t pw_batch_destroy(pw_batch_t b) {
     return PW_OK;
 }
 
-pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t ty, int32_t stages, int32_t ctas_per_sm,
-                                int32_t rows_per_thread) {
+pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
+                                int32_t ctas_per_sm, int32_t rows_per_thread) {
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
-    if (rows_per_thread < 0 || rows_per_thread > 2) return bfail(PW_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
+    if (rows_per_thread < 0 || rows_per_thread > 3)
+        return bfail(PW_ERR_ARG, "rows_per_thread must be 0, 1, 2 or 3");
     TmaConfig c{lanes_x ? lanes_x : 32, ty ? ty : 4, stages ? stages : 4, 1};
+    c.nc = cells ? cells : 4;
     c.rp = rows_per_thread ? rows_per_thread : 1;
+    if (c.rp == 3) {
+        c.rp = 1;
+        c.xp = 1;
+    }
     if (!batch_config_supported(c, b->dtype))
         return internal_fail(PW_ERR_UNSUPPORTED,
-                             "no batched kernel instance for lanes_x=%d ty=%d stages=%d rows_per_thread=%d (dtype %d)",
-                             c.lx, c.ty, c.stages, c.rp, (int)b->dtype);
+                             "no batched kernel instance for lanes_x=%d cells=%d ty=%d stages=%d rows_per_thread=%d "
+                             "(dtype %d)",
+                             c.lx, c.nc, c.ty, c.stages, rows_per_thread ? rows_per_thread : 1, (int)b->dtype);
     if (ctas_per_sm < 0) return bfail(PW_ERR_ARG, "ctas_per_sm must be >= 0");
     b->cfg = c;
     b->ctas_per_sm = ctas_per_sm;
@@ -357,6 +371,7 @@ pw_status_t pw_batch_info(pw_batch_t b, int64_t* n_items, int64_t* cells, int32_
 pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* const* v, const void* const* w,
                                 void* const* su, void* const* sv, void* const* sw, const float* scale,
                                 pw_stream_t stream) {
+    PW_RANGE("pw_batch_tendencies");
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
     if (!u || !v || !w || !su || !sv || !sw) return bfail(PW_ERR_ARG, "a pointer table is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -389,7 +404,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
             const pw_grid_t& g = b->grids[q];
             for (int a = 0; a < 3; ++a) {
                 pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->cfg.lx, b->cfg.ty,
-                                                   &b->h_maps[3 * (size_t)q + a]);
+                                                   &b->h_maps[3 * (size_t)q + a], b->cfg.nc);
                 if (st != PW_OK) return st;
             }
             BatchGridDev& r = b->h_grids[q];
@@ -401,7 +416,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
             r.g.pk = g.pitch_k;
             r.g.origin = g.origin;
             r.ox = b->ox[q];
-            r.tiles_x = (g.nx + 4 * b->cfg.lx - 1) / (4 * b->cfg.lx);
+            r.tiles_x = (g.nx + b->cfg.nc * b->cfg.lx - 1) / (b->cfg.nc * b->cfg.lx);
             r.tiles_y = (g.ny + b->cfg.ty - 1) / b->cfg.ty;
             r.nseg = 1;
             r.tcx = b->tcx[q];

@@ -7,7 +7,33 @@
 
 #include "../../include/pw.h"
 
+// NVTX ranges around the library's launching entry points, so a timeline
+// tool shows each C-ABI call by name.  NVTX v3 is header-only: with no tool
+// attached a range costs two calls of empty functions.  Build with
+// -DPW_NVTX=0 to compile them out.
+#ifndef PW_NVTX
+#define PW_NVTX 1
+#endif
+#if PW_NVTX && __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define PW_HAVE_NVTX 1
+#else
+#define PW_HAVE_NVTX 0
+#endif
+
 namespace pw {
+
+struct NvtxRange {
+#if PW_HAVE_NVTX
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char*) {}
+#endif
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define PW_RANGE(name) const ::pw::NvtxRange pw_nvtx_range_(name)
 
 // Field geometry as the kernels see it: element (k, j, i) of a field sits at
 // ptr[origin + k*pk + j*pj + i], with i in [1-halo, nx+halo], j likewise,
@@ -66,6 +92,7 @@ struct TmaConfig {
     int seg0 = 0;       // first segment to launch
     int seg_count = 0;  // segments to launch (0 = all nseg)
     int rp = 1;         // rows per thread: 1, or 2 (packed FP32x2 arithmetic on row pairs)
+    int xp = 0;         // 1: one row per thread, its nc cells packed as FP32x2 pairs (cell q, cell q + nc/2)
 };
 
 // Launch shape of the two-step (temporal blocking) k-march kernel.
@@ -153,6 +180,12 @@ cudaError_t launch_weighted_dot(pw_dtype_t dt, const GridDev& g, const void* a, 
 pw_status_t internal_fail(pw_status_t s, const char* fmt, ...);
 pw_status_t internal_cuda_fail(cudaError_t e, const char* what);
 bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
+// The GPU a handle was created on.
+int internal_handle_device(pw_handle_t h);
+// Every pointer in ps[0..n) is device memory of the handle's GPU (the same
+// check, and the same per-handle cache of checked pointers, as the field
+// arguments of every other entry point).
+pw_status_t internal_check_device_ptrs(pw_handle_t h, const void* const* ps, int n);
 
 // Layout checks and TMA descriptors shared by the single-grid and batched paths.
 pw_status_t validate_grid(const pw_grid_t* g);

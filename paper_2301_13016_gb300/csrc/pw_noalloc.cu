@@ -53,13 +53,19 @@ using namespace pw;
 extern "C" pw_status_t pw_weighted_dot_noalloc(pw_handle_t h, const void* a, float sa, const void* b, float sb,
                                                const double* wk, int32_t k0, int32_t k1, double* out,
                                                pw_stream_t stream) {
+    PW_RANGE("pw_weighted_dot_noalloc");
     pw_grid_t g;
     int num_sms = 0;
     if (!internal_handle_grid(h, &g, &num_sms)) return internal_fail(PW_ERR_ARG, "handle is NULL");
     if (!a || !b || !out) return internal_fail(PW_ERR_ARG, "a pointer is NULL");
+    const void* dp[2] = {a, b};
+    pw_status_t st = internal_check_device_ptrs(h, dp, 2);
+    if (st != PW_OK) return st;
+    // the static array's address is per device: the handle's GPU must be current
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || !is_device_ptr(a, dev) || !is_device_ptr(b, dev))
-        return internal_fail(PW_ERR_ARG, "a field pointer is not device memory of the current GPU");
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != internal_handle_device(h))
+        return internal_fail(PW_ERR_ARG, "pw_weighted_dot_noalloc: the handle's GPU %d is not the current device",
+                             internal_handle_device(h));
     if (k0 < 1 || k1 > g.nz || k0 > k1) return internal_fail(PW_ERR_ARG, "need 1 <= k0 <= k1 <= nz");
     if (g.nz + 2 > kNoallocMaxLevels)
         return internal_fail(PW_ERR_UNSUPPORTED,

@@ -27,13 +27,11 @@ struct Epilogue<T, MODE_TEND> {
         o1[o] = Store<T>::from_f(b);
         o2[o] = Store<T>::from_f(c);
     }
+    // one field's row vector of N cells
     template <int N>
-    static __device__ __forceinline__ void storevec(T* o0, T* o1, T* o2, long long o, const float (&a)[N],
-                                                    const float (&b)[N], const float (&c)[N], const GridDev&, int,
-                                                    int) {
-        storev<N>(o0 + o, a);
-        storev<N>(o1 + o, b);
-        storev<N>(o2 + o, c);
+    static __device__ __forceinline__ void store_field(T* of, long long o, const float (&a)[N], const GridDev&, int,
+                                                       int) {
+        storev<N>(of + o, a);
     }
 };
 
@@ -119,37 +117,25 @@ struct Epilogue<T, MODE_STEP> {
         o2[o] = tc;
         StepImages::cell<T>(o0, o1, o2, o, ta, tb, tc, g, j, i);
     }
-    // a vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
+    // one field's vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
     template <int N>
-    static __device__ __forceinline__ void storevec(T* o0, T* o1, T* o2, long long o, const float (&a)[N],
-                                                    const float (&b)[N], const float (&c)[N], const GridDev& g, int j,
-                                                    int i0) {
-        storev<N>(o0 + o, a);
-        storev<N>(o1 + o, b);
-        storev<N>(o2 + o, c);
+    static __device__ __forceinline__ void store_field(T* of, long long o, const float (&a)[N], const GridDev& g,
+                                                       int j, int i0) {
+        storev<N>(of + o, a);
         if (g.halo != 1) return;   // deeper halos are refreshed by the halo kernel
         const bool west = (i0 == 1), east = (i0 + N - 1 == g.nx);
         // most row vectors touch no boundary: one test, the same at every level
         if (!(west | east | (j == 1) | (j == g.ny))) return;
         const long long dyp = (j == 1) ? (long long)g.ny * g.pj : 0;
         const long long dym = (j == g.ny) ? -(long long)g.ny * g.pj : 0;
-        auto cell = [&](long long p, int q) {
-            o0[p] = Store<T>::from_f(a[q]);
-            o1[p] = Store<T>::from_f(b[q]);
-            o2[p] = Store<T>::from_f(c[q]);
-        };
         const long long shifts[3] = {0, dyp, dym};
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             if (s > 0 && shifts[s] == 0) continue;
             const long long p = o + shifts[s];
-            if (s > 0) {   // the row image
-                storev<N>(o0 + p, a);
-                storev<N>(o1 + p, b);
-                storev<N>(o2 + p, c);
-            }
-            if (west) cell(p + g.nx, 0);                   // cell i = 1 -> i = nx+1
-            if (east) cell(p + (N - 1) - g.nx, N - 1);     // cell i = nx -> i = 0
+            if (s > 0) storev<N>(of + p, a);                                   // the row image
+            if (west) of[p + g.nx] = Store<T>::from_f(a[0]);                  // cell i = 1 -> i = nx+1
+            if (east) of[p + (N - 1) - g.nx] = Store<T>::from_f(a[N - 1]);    // cell i = nx -> i = 0
         }
     }
 };
@@ -294,159 +280,322 @@ struct MarchRegs {
 
 enum { F_U = 0, F_V = 1, F_W = 2 };
 
-// Source terms (Sec. 2.2) of level kk, handed to `out`, then the roll of `st`
-// to level kk+1.  The data source is abstract:
+// x neighbours of a thread's row vector by warp shuffles: the value at x = -1
+// (m) and x = NC (p) come from the adjacent lanes, the row's two edge lanes
+// read theirs from the halo columns (edge(f, up, dr): the value beyond the
+// row's first lane for lane 0, beyond its last lane for lane LX-1).
+template <int NC, int LX, typename V, class Edge>
+struct NbrShfl {
+    const Edge& edge;
+    const int xl;
+    __device__ __forceinline__ V m(int f, int up, int dr, const V (&x)[NC]) const {
+        return VOps<V>::sel(xl == 0, edge(f, up, dr), VOps<V>::shfl_up(x[NC - 1], LX));
+    }
+    __device__ __forceinline__ V p(int f, int up, int dr, const V (&x)[NC]) const {
+        return VOps<V>::sel(xl == LX - 1, edge(f, up, dr), VOps<V>::shfl_down(x[0], LX));
+    }
+};
+
+// x neighbours when a thread's 2*NP consecutive cells are packed as NP pairs
+// (cell q, cell q + NP): the pair one cell to the left of pair 0 is
+// (x = -1, cell NP - 1) and the pair one to the right of pair NP-1 is
+// (cell NP, x = 2*NP), so each takes one value loaded from the staged row
+// (ld(f, up, dr, side): side 0 the value at x = -1, side 1 at x = 2*NP) and
+// one of the thread's own.
+template <int NP, class Ld>
+struct NbrPairs {
+    const Ld& ld;
+    __device__ __forceinline__ float2 m(int f, int up, int dr, const float2 (&x)[NP]) const {
+        return make_float2(ld(f, up, dr, 0), x[NP - 1].x);
+    }
+    __device__ __forceinline__ float2 p(int f, int up, int dr, const float2 (&x)[NP]) const {
+        return make_float2(x[0].y, ld(f, up, dr, 1));
+    }
+};
+
+// Per-level vertical coefficients of the three outputs, storage scales folded
+// in (FoldedCoef): lower tzc1*kz_u, tzc1*kz_v; upper -(tzc2*kz_u), -(tzc2*kz_v),
+// tzd1*kz_w, -(tzd2*kz_w).
+// ZCoefLdg reads the coefficient arrays every level; ZCoefTab reads a table of
+// the same products that the CTA computed once (zcoef_fill), each value
+// stored twice so that a 16-byte shared load gives two ready FP32x2 operands.
+struct ZCoefLdg {
+    const FoldedCoef& k;
+    const int nzp2;
+    template <typename V>
+    __device__ __forceinline__ void lower(int kk, V& tz1u, V& tz1v) const {
+        const float t1 = __ldg(k.tz + kk);
+        tz1u = VOps<V>::splat(t1 * k.kz[0]);
+        tz1v = VOps<V>::splat(t1 * k.kz[1]);
+    }
+    template <typename V>
+    __device__ __forceinline__ void upper(int kk, V& ntz2u, V& ntz2v, V& td1w, V& ntd2w) const {
+        const float t2 = __ldg(k.tz + nzp2 + kk);
+        const float d1 = __ldg(k.tz + 2 * nzp2 + kk);
+        const float d2 = __ldg(k.tz + 3 * nzp2 + kk);
+        ntz2u = VOps<V>::splat(-(t2 * k.kz[0]));
+        ntz2v = VOps<V>::splat(-(t2 * k.kz[1]));
+        td1w = VOps<V>::splat(d1 * k.kz[2]);
+        ntd2w = VOps<V>::splat(-(d2 * k.kz[2]));
+    }
+};
+
+struct ZCoefTab {
+    const float4* tab;   // 3 float4 per level, level `base` first
+    int base;
+    static __device__ __forceinline__ void get(const float4& a, float& x, float& y) {
+        x = a.x;
+        y = a.z;
+    }
+    static __device__ __forceinline__ void get(const float4& a, float2& x, float2& y) {
+        x = make_float2(a.x, a.y);
+        y = make_float2(a.z, a.w);
+    }
+    template <typename V>
+    __device__ __forceinline__ void lower(int kk, V& tz1u, V& tz1v) const {
+        get(tab[3 * (kk - base)], tz1u, tz1v);
+    }
+    template <typename V>
+    __device__ __forceinline__ void upper(int kk, V& ntz2u, V& ntz2v, V& td1w, V& ntd2w) const {
+        get(tab[3 * (kk - base) + 1], ntz2u, ntz2v);
+        get(tab[3 * (kk - base) + 2], td1w, ntd2w);
+    }
+};
+
+// Levels lo..hi of the ZCoefTab table (entry 0 = level lo), computed by all
+// `nthreads` threads of the CTA (the caller then synchronises the CTA).
+__device__ __forceinline__ void zcoef_fill(float4* tab, const FoldedCoef& k, const int nzp2, const int lo,
+                                           const int hi, const int tid, const int nthreads) {
+    for (int e = tid; e < 3 * (hi - lo + 1); e += nthreads) {
+        const int kk = lo + e / 3, part = e - 3 * (e / 3);
+        float a, b;
+        if (part == 0) {
+            const float t1 = __ldg(k.tz + kk);
+            a = t1 * k.kz[0];
+            b = t1 * k.kz[1];
+        } else if (part == 1) {
+            const float t2 = __ldg(k.tz + nzp2 + kk);
+            a = -(t2 * k.kz[0]);
+            b = -(t2 * k.kz[1]);
+        } else {
+            const float d1 = __ldg(k.tz + 2 * nzp2 + kk), d2 = __ldg(k.tz + 3 * nzp2 + kk);
+            a = d1 * k.kz[2];
+            b = -(d2 * k.kz[2]);
+        }
+        tab[e] = make_float4(a, a, b, b);
+    }
+}
+
+// Source terms (Sec. 2.2) of level kk, handed to `out` one field at a time,
+// then the roll of `st` to level kk+1.  The data sources are abstract:
 //   row(f, up, dr, o)  the thread's NC values of field f (F_U, F_V, F_W) in
 //                      row r+dr of level kk+up (up = 0 or 1)
-//   edge(f, up, dr)    the x neighbour beyond the row's ends: x = -1 for the
-//                      row's first lane, x = NC*LX for its last lane
-//   out(ru, rv, rw, u, v, w)   the source terms and the level-kk values
+//   nbr.m / nbr.p      the value one cell beyond the row vector on the left
+//                      (x = -1) / right (x = NC) (NbrShfl, NbrPairs)
+//   zc                 the per-level vertical coefficients (ZCoefLdg, ZCoefTab)
+//   out(f, s, q)       the source term s of field f and the field's level-kk
+//                      values q
 // first:   kk is the first level of the march (its rows are loaded here)
 // have_up: level kk+1 exists (kk < nz): the upper vertical fluxes and sw
 // compute: evaluate the source terms (else they are zero: k = 1, or a level
 //          that only primes the carried state)
-// x neighbours within a row come from the adjacent lanes by warp shuffles
-// (LX lanes per row).  Pair sums along x are shared by neighbouring cells.
-template <int NC, int LX, typename V, class Row, class Edge, class Out>
-__device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row, const Edge& edge, const Out& out,
-                                            const int xl, const bool first, const bool have_up, const bool compute,
-                                            const FoldedCoef& k, const int kk, const int nzp2) {
+// The fields go one after the other (su, then sv, then sw, each handed out
+// as soon as it is complete, and each lower flux product of the next level
+// formed as soon as its pair sum has had its last use), so that few values
+// are live at once.  Pair sums along x are shared by neighbouring cells.
+// Every form of the k-march runs this one sequence of operations, so they
+// agree bit for bit.
+template <int NC, typename V, class Row, class Nbr, class ZC, class Out>
+__device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row& row, const Nbr& nbr, const ZC& zc,
+                                                 const Out& out, const bool first, const bool have_up,
+                                                 const bool compute, const FoldedCoef& k, const int kk) {
     using O = VOps<V>;
-    // x-neighbours of a row vector: value at x = -1 (m) and x = NC (p)
-    auto nbr_m = [&](const V (&x)[NC], V e) { return O::sel(xl == 0, e, O::shfl_up(x[NC - 1], LX)); };
-    auto nbr_p = [&](const V (&x)[NC], V e) { return O::sel(xl == LX - 1, e, O::shfl_down(x[0], LX)); };
     if (first) {
         row(F_U, 0, 0, st.u0);
         row(F_V, 0, 0, st.v0);
         row(F_V, 0, -1, st.vs);
         row(F_W, 0, 0, st.w0);
     }
-    V wn[NC];
-    row(F_W, 0, 1, wn);
-    const V ew = edge(F_W, 0, 0);
-    V W[NC + 2];   // x = -1..NC
-    W[0] = nbr_m(st.w0, ew);
-    W[NC + 1] = nbr_p(st.w0, ew);
+    V W[NC + 2];   // w of level kk, x = -1..NC
+    W[0] = nbr.m(F_W, 0, 0, st.w0);
+    W[NC + 1] = nbr.p(F_W, 0, 0, st.w0);
 #pragma unroll
     for (int c = 0; c < NC; ++c) W[c + 1] = st.w0[c];
-
+    // upper vertical pair sum of su at level kk = its lower one at kk+1
+    V pzu_n[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pzu_n[c] = O::add(W[c + 1], W[c + 2]);   // w(k,i) + w(k,i+1)
     // level kk+1 rows (upper terms; carried into the next step)
     V uu[NC], vu[NC], vus[NC], wu[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) uu[c] = vu[c] = vus[c] = wu[c] = O::zero();
-    V euu = O::zero();
-    if (have_up) {
-        row(F_U, 1, 0, uu);
-        row(F_V, 1, 0, vu);
-        row(F_V, 1, -1, vus);
-        row(F_W, 1, 0, wu);
-        euu = edge(F_U, 1, 0);
-    }
-    // upper vertical pair sums of level kk = lower ones of level kk+1
-    V pzu_n[NC], pzv_n[NC], pzw_n[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        pzu_n[c] = O::add(W[c + 1], W[c + 2]);   // w(k,i) + w(k,i+1)
-        pzv_n[c] = O::add(st.w0[c], wn[c]);      // w(k,j) + w(k,j+1)
-        pzw_n[c] = O::add(st.w0[c], wu[c]);      // w(k) + w(k+1)
-    }
+    if (have_up) row(F_U, 1, 0, uu);
 
-    V ru[NC], rv[NC], rw[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) ru[c] = rv[c] = rw[c] = O::zero();
+    V r[NC];   // the source term of the field in hand
     if (compute) {
         // per output field: x, y and lower vertical coefficients (storage scales folded in)
         const V kxu = O::splat(k.kx[0]), kxv = O::splat(k.kx[1]), kxw = O::splat(k.kx[2]);
         const V kyu = O::splat(k.ky[0]), kyv = O::splat(k.ky[1]), kyw = O::splat(k.ky[2]);
-        V us[NC], un[NC], vn[NC], ws[NC];
-        row(F_U, 0, -1, us);
-        row(F_U, 0, 1, un);
-        row(F_V, 0, 1, vn);
-        row(F_W, 0, -1, ws);
-        const V eu = edge(F_U, 0, 0);
-        const V ev = edge(F_V, 0, 0);
-        const V eun = edge(F_U, 0, 1);
-        const V evs = edge(F_V, 0, -1);
+        V tz1u, tz1v, ntz2u = O::zero(), ntz2v = O::zero(), td1w = O::zero(), ntd2w = O::zero();
+        zc.lower(kk, tz1u, tz1v);
+        if (have_up) zc.upper(kk, ntz2u, ntz2v, td1w, ntd2w);
+
+        // ---- su
         V U[NC + 2], Vv[NC + 2];   // x = -1..NC
-        V UN[NC + 1], UU[NC + 1];  // x = -1..NC-1
         V VS[NC + 1];              // x = 0..NC
-        U[0] = nbr_m(st.u0, eu);
-        U[NC + 1] = nbr_p(st.u0, eu);
-        Vv[0] = nbr_m(st.v0, ev);
-        Vv[NC + 1] = nbr_p(st.v0, ev);
-        UN[0] = nbr_m(un, eun);
-        UU[0] = nbr_m(uu, euu);
-        VS[NC] = nbr_p(st.vs, evs);
+        U[0] = nbr.m(F_U, 0, 0, st.u0);
+        U[NC + 1] = nbr.p(F_U, 0, 0, st.u0);
+        Vv[0] = nbr.m(F_V, 0, 0, st.v0);
+        Vv[NC + 1] = nbr.p(F_V, 0, 0, st.v0);
+        VS[NC] = nbr.p(F_V, 0, -1, st.vs);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             U[c + 1] = st.u0[c];
             Vv[c + 1] = st.v0[c];
-            UN[c + 1] = un[c];
-            UU[c + 1] = uu[c];
             VS[c] = st.vs[c];
         }
-
-        // pair sums along x shared by neighbouring cells: index c is the
-        // pair (x = c-1, c)
-        V pxu[NC + 1], qx[NC + 1], rx[NC + 1], pxv[NC], pys[NC];
+        V un[NC];
+        row(F_U, 0, 1, un);
+        {
+            V us[NC];
+            row(F_U, 0, -1, us);
+            // pair sums along x shared by neighbouring cells: index c is the
+            // pair (x = c-1, c)
+            V pxu[NC + 1], pxv[NC], pys[NC];
 #pragma unroll
-        for (int c = 0; c < NC + 1; ++c) {
-            pxu[c] = O::add(U[c], U[c + 1]);   // u(i-1) + u(i)
-            qx[c] = O::add(U[c], UN[c]);       // u(j,i-1) + u(j+1,i-1)
-            rx[c] = O::add(U[c], UU[c]);       // u(k,i-1) + u(k+1,i-1)
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            pxv[c] = O::add(Vv[c + 1], Vv[c + 2]);   // v(j,i) + v(j,i+1)
-            pys[c] = O::add(VS[c], VS[c + 1]);       // v(j-1,i) + v(j-1,i+1)
-        }
-        const float t1 = __ldg(k.tz + kk);
-        const V tz1u = O::splat(t1 * k.kz[0]), tz1v = O::splat(t1 * k.kz[1]);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            // su
-            V x = O::mul(kxu, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
-            x = O::fma(kyu, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
-            ru[c] = O::fma(tz1u, st.pdu[c], x);
-            // sv
-            V y = O::mul(kxv, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
-            y = O::fma(kyv,
-                       O::fma(O::neg(vn[c]), O::add(Vv[c + 1], vn[c]), O::mul(st.vs[c], O::add(Vv[c + 1], st.vs[c]))),
-                       y);
-            rv[c] = O::fma(tz1v, st.pdv[c], y);
-        }
-        if (have_up) {   // kk < nz: upper vertical fluxes and sw
-            const float t2 = __ldg(k.tz + nzp2 + kk);
-            const float d1 = __ldg(k.tz + 2 * nzp2 + kk);
-            const float d2 = __ldg(k.tz + 3 * nzp2 + kk);
-            const V ntz2u = O::splat(-(t2 * k.kz[0])), ntz2v = O::splat(-(t2 * k.kz[1]));
-            const V td1w = O::splat(d1 * k.kz[2]), ntd2w = O::splat(-(d2 * k.kz[2]));
+            for (int c = 0; c < NC + 1; ++c) pxu[c] = O::add(U[c], U[c + 1]);   // u(i-1) + u(i)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                ru[c] = O::fma(ntz2u, O::mul(uu[c], pzu_n[c]), ru[c]);
-                rv[c] = O::fma(ntz2v, O::mul(vu[c], pzv_n[c]), rv[c]);
+                pxv[c] = O::add(Vv[c + 1], Vv[c + 2]);   // v(j,i) + v(j,i+1)
+                pys[c] = O::add(VS[c], VS[c + 1]);       // v(j-1,i) + v(j-1,i+1)
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                V x = O::mul(kxu, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
+                x = O::fma(kyu, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
+                r[c] = O::fma(tz1u, st.pdu[c], x);
+                if (have_up) r[c] = O::fma(ntz2u, O::mul(uu[c], pzu_n[c]), r[c]);
+            }
+        }
+        out(F_U, r, st.u0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st.pdu[c] = O::mul(st.u0[c], pzu_n[c]);   // u(k) * (w(k,i) + w(k,i+1))
+
+        // ---- sv
+        V wn[NC];
+        row(F_W, 0, 1, wn);
+        V pzv_n[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) pzv_n[c] = O::add(st.w0[c], wn[c]);   // w(k,j) + w(k,j+1)
+        if (have_up) row(F_V, 1, 0, vu);
+        {
+            V vn[NC];
+            row(F_V, 0, 1, vn);
+            V UN[NC + 1], qx[NC + 1];   // x = -1..NC-1
+            UN[0] = nbr.m(F_U, 0, 1, un);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) UN[c + 1] = un[c];
+#pragma unroll
+            for (int c = 0; c < NC + 1; ++c) qx[c] = O::add(U[c], UN[c]);   // u(j,i-1) + u(j+1,i-1)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                V y = O::mul(kxv, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
+                y = O::fma(kyv,
+                           O::fma(O::neg(vn[c]), O::add(Vv[c + 1], vn[c]),
+                                  O::mul(st.vs[c], O::add(Vv[c + 1], st.vs[c]))),
+                           y);
+                r[c] = O::fma(tz1v, st.pdv[c], y);
+                if (have_up) r[c] = O::fma(ntz2v, O::mul(vu[c], pzv_n[c]), r[c]);
+            }
+        }
+        out(F_V, r, st.v0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st.pdv[c] = O::mul(st.v0[c], pzv_n[c]);   // v(k) * (w(k,j) + w(k,j+1))
+
+        // ---- sw (zero at the lid)
+        if (have_up) {
+            row(F_V, 1, -1, vus);
+            row(F_W, 1, 0, wu);
+        }
+        V pzw_n[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            pzw_n[c] = O::add(st.w0[c], wu[c]);   // w(k) + w(k+1)
+            r[c] = O::zero();
+        }
+        if (have_up) {
+            V ws[NC];
+            row(F_W, 0, -1, ws);
+            V UU[NC + 1], rx[NC + 1];   // x = -1..NC-1
+            UU[0] = nbr.m(F_U, 1, 0, uu);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) UU[c + 1] = uu[c];
+#pragma unroll
+            for (int c = 0; c < NC + 1; ++c) rx[c] = O::add(U[c], UU[c]);   // u(k,i-1) + u(k+1,i-1)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
                 V z = O::mul(kxw, O::fma(O::neg(W[c + 2]), rx[c + 1], O::mul(W[c], rx[c])));
                 z = O::fma(kyw, O::fma(O::neg(wn[c]), O::add(Vv[c + 1], vu[c]), O::mul(ws[c], O::add(st.vs[c], vus[c]))),
                            z);
                 z = O::fma(td1w, st.pdw[c], z);
-                rw[c] = O::fma(ntd2w, O::mul(wu[c], pzw_n[c]), z);
+                r[c] = O::fma(ntd2w, O::mul(wu[c], pzw_n[c]), z);
             }
+        }
+        out(F_W, r, st.w0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st.pdw[c] = O::mul(st.w0[c], pzw_n[c]);   // w(k) * (w(k) + w(k+1))
+    } else {
+        // no source terms at this level: zeros out, and the rows and flux
+        // products of level kk+1
+        V wn[NC];
+        row(F_W, 0, 1, wn);
+        if (have_up) {
+            row(F_V, 1, 0, vu);
+            row(F_V, 1, -1, vus);
+            row(F_W, 1, 0, wu);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) r[c] = O::zero();
+        out(F_U, r, st.u0);
+        out(F_V, r, st.v0);
+        out(F_W, r, st.w0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            st.pdu[c] = O::mul(st.u0[c], pzu_n[c]);
+            st.pdv[c] = O::mul(st.v0[c], O::add(st.w0[c], wn[c]));
+            st.pdw[c] = O::mul(st.w0[c], O::add(st.w0[c], wu[c]));
         }
     }
 
-    out(ru, rv, rw, st.u0, st.v0, st.w0);
-
-    // roll: the lower flux products of level kk+1, then level kk+1 becomes level kk
+    // roll: level kk+1 becomes level kk
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        st.pdu[c] = O::mul(st.u0[c], pzu_n[c]);   // u(k) * (w(k,i) + w(k,i+1))
-        st.pdv[c] = O::mul(st.v0[c], pzv_n[c]);   // v(k) * (w(k,j) + w(k,j+1))
-        st.pdw[c] = O::mul(st.w0[c], pzw_n[c]);   // w(k) * (w(k) + w(k+1))
         st.u0[c] = uu[c];
         st.v0[c] = vu[c];
         st.vs[c] = vus[c];
         st.w0[c] = wu[c];
     }
+}
+
+// The k-march level with x neighbours by warp shuffles (LX lanes per row) and
+// the vertical coefficients read each level (the two-step kernel's stages):
+// out(ru, rv, rw, u, v, w) receives the three source terms together.
+template <int NC, int LX, typename V, class Row, class Edge, class Out>
+__device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row, const Edge& edge, const Out& out,
+                                            const int xl, const bool first, const bool have_up, const bool compute,
+                                            const FoldedCoef& k, const int kk, const int nzp2) {
+    const NbrShfl<NC, LX, V, Edge> nbr{edge, xl};
+    const ZCoefLdg zc{k, nzp2};
+    V ru[NC], rv[NC];
+    auto out3 = [&](int f, const V (&r)[NC], const V (&)[NC]) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (f == F_U) ru[c] = r[c];
+            if (f == F_V) rv[c] = r[c];
+        }
+        if (f == F_W) out(ru, rv, r, st.u0, st.v0, st.w0);
+    };
+    march_level_core<NC, V>(st, row, nbr, zc, out3, first, have_up, compute, k, kk);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,28 +627,6 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 // Ring bookkeeping is global to the CTA: the n-th plane a CTA ever issues
 // goes to slot n % S and completes phase (n / S) & 1 of that slot's mbarrier,
 // so a persistent CTA can march tile after tile without re-initialising.
-template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1>
-struct TmaLayout {
-    static constexpr int TX = NC * LX;
-    static constexpr int RPW = 32 / LX;                // thread rows per warp
-    static constexpr int WARPS = TY / (RPW * RP);
-    static constexpr int THREADS = 32 * WARPS;
-    static constexpr int PADX = 16 / (int)sizeof(T);   // elements in one 16-byte granule
-    static constexpr int BW = TX + 2 * PADX;           // box width
-    static constexpr int ROWS = TY + 2;
-    static constexpr int FIELD_RAW = BW * ROWS;
-    static constexpr int FIELD_BYTES = ((FIELD_RAW * (int)sizeof(T) + 127) / 128) * 128;
-    static constexpr int FIELD = FIELD_BYTES / (int)sizeof(T);
-    static constexpr int STAGE = 3 * FIELD;
-    static constexpr uint32_t TX_BYTES = 3u * FIELD_RAW * (uint32_t)sizeof(T);
-    static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16 + 4 * S;
-    static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
-    static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
-    static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
-    static_assert(TY % (RPW * RP) == 0, "TY must be a multiple of the rows per warp");
-    static_assert(RP == 1 || RP == 2, "one or two rows per thread");
-};
-
 // Build-time knob of the k-march kernel: PW_TMA_MAX_MINB caps the resident
 // CTAs per SM the register budget of the 4-cell shapes is sized for.  On
 // GB300 a cap of 2 (the compiler's own choice, about 128 registers) was the
@@ -521,6 +648,54 @@ struct TmaLayout {
 #ifndef PW_MARCH_SPLIT_ARRIVE
 #define PW_MARCH_SPLIT_ARRIVE 0
 #endif
+// Levels per iteration of the k-march loop (2: the carried rows of one level
+// are renamed rather than moved into place for the next).
+#ifndef PW_MARCH_UNROLL
+#define PW_MARCH_UNROLL 1
+#endif
+#ifndef PW_MARCH_UNROLL_XP
+#define PW_MARCH_UNROLL_XP 2
+#endif
+// Steady levels with their facts (not first, computing, level kk+1 exists)
+// as compile-time constants (0: the same runtime tests as other levels).
+#ifndef PW_MARCH_FAST
+#define PW_MARCH_FAST 1
+#endif
+// x-pair form: staged rows read through explicit 32-bit shared addresses
+// (with two levels per iteration: BF16 384 against 376 Gcell/s at 2048^2 x 64).
+#ifndef PW_MARCH_LDS_ASM
+#define PW_MARCH_LDS_ASM 1
+#endif
+
+template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1, int XP = 0>
+struct TmaLayout {
+    static constexpr int TX = NC * LX;
+    static constexpr int RPW = 32 / LX;                // thread rows per warp
+    static constexpr int WARPS = TY / (RPW * RP);
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int PADX = 16 / (int)sizeof(T);   // elements in one 16-byte granule
+    static constexpr int BW = TX + 2 * PADX;           // box width
+    static constexpr int ROWS = TY + 2;
+    static constexpr int FIELD_RAW = BW * ROWS;
+    static constexpr int FIELD_BYTES = ((FIELD_RAW * (int)sizeof(T) + 127) / 128) * 128;
+    static constexpr int FIELD = FIELD_BYTES / (int)sizeof(T);
+    static constexpr int STAGE = 3 * FIELD;
+    static constexpr uint32_t TX_BYTES = 3u * FIELD_RAW * (uint32_t)sizeof(T);
+    // packed FP32x2 forms read the per-level vertical coefficients from a
+    // table in shared memory (ZCoefTab), CTAB_LEVELS levels at a time
+    static constexpr bool PACKED = (RP == 2 || XP == 1);
+    static constexpr bool CTAB = PACKED;
+    static constexpr int CTAB_LEVELS = 128;
+    static constexpr size_t CTAB_OFF =
+        (((size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16 + 4 * S + 15) / 16) * 16;
+    static constexpr size_t SMEM = CTAB_OFF + (CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0);
+    static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
+    static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
+    static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
+    static_assert(TY % (RPW * RP) == 0, "TY must be a multiple of the rows per warp");
+    static_assert(RP == 1 || RP == 2, "one or two rows per thread");
+    static_assert(XP == 0 || (RP == 1 && sizeof(T) == 2), "x pairs: one row per thread, 16-bit storage");
+};
 
 // Resident CTAs per SM the register budget is sized for: what shared memory
 // and the thread limit allow, at most PW_TMA_MAX_MINB for 4 cells a thread;
@@ -528,9 +703,9 @@ struct TmaLayout {
 // measured best on GB300 (16 lanes x 8 cells x 4 rows: 269 -> 295 Gcell/s for
 // BF16 against the compiler's 210 registers, as more CTAs per SM hide more
 // latency; 128 spills and 200 leaves 2 CTAs per SM, both slower).
-template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1>
+template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1, int XP = 0>
 constexpr int tma_min_blocks() {
-    using L = TmaLayout<T, LX, TY, S, NC, RP>;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
     constexpr int by_regs = NC * RP == 8 ? 65536 / (L::THREADS * PW_TMA_REGS8) : PW_TMA_MAX_MINB;
@@ -541,18 +716,20 @@ constexpr int tma_min_blocks() {
 
 // Shared memory of a k-march CTA: the plane ring, one mbarrier per slot, the
 // flags and one release counter per slot.
-template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1>
+template <typename T, int LX, int TY, int S, int NC = 4, int RP = 1, int XP = 0>
 struct MarchSmem {
-    using L = TmaLayout<T, LX, TY, S, NC, RP>;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
     T* stages;
     uint64_t* bars;
     volatile int* flag;   // [0] abort, [1] work item broadcast, [2] planes issued (highest + 1)
     uint32_t* cnt;        // warps done with each slot's plane
+    float4* ctab;         // vertical coefficient table (L::CTAB)
     __device__ __forceinline__ MarchSmem(unsigned char* raw) {
         stages = reinterpret_cast<T*>(raw);
         bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * L::STAGE * sizeof(T));
         flag = reinterpret_cast<volatile int*>(bars + S);
         cnt = reinterpret_cast<uint32_t*>(bars + S) + 4;
+        ctab = reinterpret_cast<float4*>(raw + L::CTAB_OFF);
     }
     // one thread, then a CTA barrier
     __device__ __forceinline__ void init(int tid) {
@@ -568,18 +745,80 @@ struct MarchSmem {
     }
 };
 
+// The thread's NC consecutive 16-bit values at p (aligned to NC elements) as
+// NC/2 FP32 pairs (value q, value q + NC/2): the pairing of the x-pair form.
+template <typename T>
+__device__ __forceinline__ float lo_f(uint32_t w) {
+    if constexpr (std::is_same<T, __half>::value)
+        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    else
+        return __uint_as_float(w << 16);
+}
+template <typename T>
+__device__ __forceinline__ float hi_f(uint32_t w) {
+    if constexpr (std::is_same<T, __half>::value)
+        return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    else
+        return __uint_as_float(w & 0xffff0000u);
+}
+template <int NC, typename T>
+__device__ __forceinline__ void unpack_pairs(const uint32_t (&w)[NC / 2], float2 (&o)[NC / 2]) {
+    constexpr int NP = NC / 2;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        // value q sits in word q/2, value q + NP in word (q + NP)/2, the same half
+        const uint32_t a = w[q / 2], b = w[(q + NP) / 2];
+        o[q] = (q & 1) ? make_float2(hi_f<T>(a), hi_f<T>(b)) : make_float2(lo_f<T>(a), lo_f<T>(b));
+    }
+}
+template <int NC, typename T>
+__device__ __forceinline__ void load_pairs(const T* p, float2 (&o)[NC / 2]) {
+    static_assert(sizeof(T) == 2 && (NC == 4 || NC == 8), "16-bit storage, 4 or 8 values");
+    uint32_t w[NC / 2];
+    if constexpr (NC == 8) {
+        const uint4 t = *reinterpret_cast<const uint4*>(p);
+        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+    } else {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+        w[0] = t.x; w[1] = t.y;
+    }
+    unpack_pairs<NC, T>(w, o);
+}
+// The same from a 32-bit shared-memory address.
+template <int NC, typename T>
+__device__ __forceinline__ void load_pairs_sa(uint32_t a, float2 (&o)[NC / 2]) {
+    static_assert(sizeof(T) == 2 && (NC == 4 || NC == 8), "16-bit storage, 4 or 8 values");
+    uint32_t w[NC / 2];
+    if constexpr (NC == 8) {
+        const uint4 t = lds_u128(a);
+        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+    } else {
+        const uint2 t = lds_u64(a);
+        w[0] = t.x; w[1] = t.y;
+    }
+    unpack_pairs<NC, T>(w, o);
+}
+
 // March one tile: columns bx, rows by, output levels kb..ke of grid g.
 // `ring` counts the planes this CTA issued before; it is advanced by the
 // planes of this tile.  Returns false if a wait timed out (the error is
 // recorded and the copies in flight are drained).
-template <typename T, int LX, int TY, int S, int MODE, int NC = 4, int RP = 1>
-__device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>& sm, const CUtensorMap* tm_u,
+//
+// Per-thread forms: RP = 1, XP = 0: NC cells of one row, scalar FP32;
+// RP = 2: the same NC cells in two adjacent rows, each cell paired with the
+// cell below it (packed FP32x2); XP = 1 (16-bit storage): NC cells of one row
+// packed as NC/2 pairs (cell q, cell q + NC/2), so that a staged row unpacks
+// straight into FP32x2 operands and the x neighbours beyond the vector come
+// from the staged row itself.
+template <typename T, int LX, int TY, int S, int MODE, int NC = 4, int RP = 1, int XP = 0>
+__device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP, XP>& sm, const CUtensorMap* tm_u,
                                            const CUtensorMap* tm_v, const CUtensorMap* tm_w, T* __restrict__ o0,
                                            T* __restrict__ o1, T* __restrict__ o2, const GridDev& g, const int ox,
                                            const FoldedCoef& kc, const float dt, const int bx, const int by,
                                            const int kb, const int ke, uint32_t& ring, int* __restrict__ err) {
-    using L = TmaLayout<T, LX, TY, S, NC, RP>;
-    using V = typename std::conditional<RP == 1, float, float2>::type;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
+    using V = typename std::conditional<L::PACKED, float2, float>::type;
+    constexpr int NV = XP ? NC / 2 : NC;   // values of type V per row vector
     constexpr int BW = L::BW;
     constexpr int PADX = L::PADX;
     constexpr int FU = 0, FV = L::FIELD, FW = 2 * L::FIELD;
@@ -621,6 +860,14 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
         for (; issued < S && issued < np; ++issued) issue(issued);
         sm.flag[2] = issued;
     }
+    // vertical coefficients of the tile's first CTAB_LEVELS levels (the
+    // previous tile of a persistent CTA is done with the table: every thread
+    // has passed its last level's barrier)
+    int tbase = pb;
+    if constexpr (L::CTAB) {
+        zcoef_fill(sm.ctab, kc, nz + 2, pb, min(ke, pb + L::CTAB_LEVELS - 1), tid, L::THREADS);
+        __syncthreads();
+    }
 
     const int r = row + 1;
     const int c0 = NC * xl + PADX;
@@ -639,16 +886,31 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
     auto ld = [&](const T* p, float (&o)[NC]) { loadv<NC>(p, o); };
     auto ld1 = [&](const T* p) { return Store<T>::to_f(*p); };
 
-    MarchRegs<NC, V> st;
+    MarchRegs<NV, V> st;
     st.zero();
     int waited = 0;   // planes 0..waited-1 are known complete
     int lp = 0;       // plane index of the level being marched
 
     // the staged planes of level kk (up = 0) and kk+1 (up = 1); with RP = 2
     // each value pairs row r+dr (x) with row r+dr+1 (y)
-    auto rowld = [&](int f, int up, int dr, V (&o)[NC]) {
-        const T* P = stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + c0;
-        if constexpr (RP == 1) {
+    auto rowp = [&](int f, int up, int dr) {
+        return stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + c0;
+    };
+    // x-pair form with PW_MARCH_LDS_ASM: 32-bit shared addresses, the
+    // thread's part added once, each load's constant part foldable into the
+    // load instruction's immediate offset
+    const uint32_t tsa = smem_u32(stages) + (uint32_t)((r * BW + c0) * (int)sizeof(T));
+    auto rowsa = [&](int f, int up, int dr) {
+        return tsa + (uint32_t)(slot(lp + up) * (L::STAGE * (int)sizeof(T))) +
+               (uint32_t)((f * L::FIELD + dr * BW) * (int)sizeof(T));
+    };
+    auto rowld = [&](int f, int up, int dr, V (&o)[NV]) {
+        const T* P = rowp(f, up, dr);
+        if constexpr (XP && PW_MARCH_LDS_ASM) {
+            load_pairs_sa<NC, T>(rowsa(f, up, dr), o);
+        } else if constexpr (XP) {
+            load_pairs<NC>(P, o);
+        } else if constexpr (RP == 1) {
             ld(P, o);
         } else {
             float a[NC], b[NC];
@@ -658,59 +920,106 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
             for (int q = 0; q < NC; ++q) o[q] = make_float2(a[q], b[q]);
         }
     };
-    auto edgeld = [&](int f, int up, int dr) -> V {
+    auto edgeld = [&](int f, int up, int dr) -> V {   // (not used by the x-pair form)
         const T* P = stages + slot(lp + up) * L::STAGE + f * L::FIELD + (r + dr) * BW + ce;
-        if constexpr (RP == 1)
+        if constexpr (XP)
+            return VOps<V>::zero();
+        else if constexpr (RP == 1)
             return ld1(P);
         else
             return make_float2(ld1(P), ld1(P + BW));
     };
+    // x-pair form: the values just beyond the thread's vector, x = -1 (side 0)
+    // and x = NC (side 1), read from the staged row
+    auto nbrld = [&](int f, int up, int dr, int side) -> float {
+        if constexpr (XP && PW_MARCH_LDS_ASM) {
+            const uint32_t x = lds_u16(rowsa(f, up, dr) + (side ? NC * (int)sizeof(T) : -(int)sizeof(T)));
+            return lo_f<T>(x);
+        } else {
+            const T* P = rowp(f, up, dr);
+            return ld1(side ? P + NC : P - 1);
+        }
+    };
 
-    // One level of the march.  Returns false on abort.
-    auto level = [&](const int kk) -> bool {
+    // One level of the march.  Returns false on abort.  FAST: a level that is
+    // neither the tile's first nor the top of the grid (its rows come from the
+    // last level, it computes, and level kk+1 exists), with those facts
+    // compile-time constants.
+    auto level = [&](const int kk, auto fast) -> bool {
+        constexpr bool FAST = decltype(fast)::value;
         lp = kk - pb;
+        if constexpr (L::CTAB) {
+            if (lp > 0 && lp % L::CTAB_LEVELS == 0) {
+                __syncthreads();   // every warp is done with the table's last level
+                tbase = kk;
+                zcoef_fill(sm.ctab, kc, nzp2, kk, min(ke, kk + L::CTAB_LEVELS - 1), tid, L::THREADS);
+                __syncthreads();
+            }
+        }
         bool ok = true;
-        if (lp == 0) ok = mbar_wait_bounded(&bars[slot(0)], parity(0), kWaitLimitNs);
-        const bool have_up = (kk + 1 <= pe);
+        if (!FAST && lp == 0) ok = mbar_wait_bounded(&bars[slot(0)], parity(0), kWaitLimitNs);
+        const bool have_up = FAST || (kk + 1 <= pe);
         if (ok && have_up) ok = mbar_wait_bounded(&bars[slot(lp + 1)], parity(lp + 1), kWaitLimitNs);
         ok = __all_sync(FULL, ok);
         if (!ok) *abort_flag = 1;
         if (ok) {
             waited = lp + (have_up ? 2 : 1);
-            // one row of outputs (values of row `half` of each V)
-            auto out_row = [&](const V (&ru)[NC], const V (&rv)[NC], const V (&rw)[NC], const V (&u0)[NC],
-                               const V (&v0)[NC], const V (&w0)[NC], const int half) {
-                auto comp = [&](const V& x) -> float {
-                    if constexpr (RP == 1)
-                        return x;
-                    else
-                        return half ? x.y : x.x;
-                };
-                float a[NC], b[NC], d[NC];
+            // the value of cell c (0..NC-1) in row `half` of the thread's vector
+            auto cellv = [&](const V (&x)[NV], const int c, const int half) -> float {
+                if constexpr (XP)
+                    return c < NV ? x[c].x : x[c - NV].y;
+                else if constexpr (RP == 1)
+                    return x[c];
+                else
+                    return half ? x[c].y : x[c].x;
+            };
+            // one field's outputs: row `half` of each V (its source terms, or
+            // with MODE_STEP the new state q + dt*s)
+            auto outf = [&](const int f, const V (&rr)[NV], const V (&q)[NV]) {
+                if (!FAST && kk < kb) return;
+                T* const of = f == F_U ? o0 : (f == F_V ? o1 : o2);
+                auto field_row = [&](const int half) {
+                    float a[NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    if (MODE == MODE_STEP) {   // at kk = 1 the source terms are 0
-                        a[c] = fmaf(dt, comp(ru[c]), comp(u0[c]));
-                        b[c] = fmaf(dt, comp(rv[c]), comp(v0[c]));
-                        d[c] = fmaf(dt, comp(rw[c]), comp(w0[c]));
-                    } else {
-                        a[c] = comp(ru[c]);
-                        b[c] = comp(rv[c]);
-                        d[c] = comp(rw[c]);
+                    for (int c = 0; c < NC; ++c)   // at kk = 1 the source terms are 0
+                        a[c] = MODE == MODE_STEP ? fmaf(dt, cellv(rr, c, half), cellv(q, c, half))
+                                                 : cellv(rr, c, half);
+                    const long long o = row_off + (long long)half * g.pj + (long long)kk * g.pk;
+                    if constexpr (MODE == MODE_TEND && NC == 8) {
+                        // nx = 4 mod 8: the row's last vector holds 4 cells of
+                        // the grid (the other 4 were computed from halo and
+                        // padding columns and are not stored)
+                        if (i0 + NC - 1 > g.nx) {
+                            const float h4[4] = {a[0], a[1], a[2], a[3]};
+                            storev<4>(of + o, h4);
+                            return;
+                        }
                     }
+                    Epilogue<T, MODE>::template store_field<NC>(of, o, a, g, j + half, i0);
+                };
+                if (valid) field_row(0);
+                if (RP == 2 && valid2) field_row(1);
+            };
+            // the same for the two-step kernel's three-field interface
+            auto out = [&](const V (&ru)[NV], const V (&rv)[NV], const V (&rw)[NV], const V (&u0)[NV],
+                           const V (&v0)[NV], const V (&w0)[NV]) {
+                outf(F_U, ru, u0);
+                outf(F_V, rv, v0);
+                outf(F_W, rw, w0);
+            };
+            const bool first = !FAST && lp == 0, compute = FAST || ((kk >= kb) && (kk >= 2));
+            if constexpr (L::CTAB) {
+                const ZCoefTab zc{sm.ctab, tbase};
+                if constexpr (XP) {
+                    const NbrPairs<NV, decltype(nbrld)> nbr{nbrld};
+                    march_level_core<NV, V>(st, rowld, nbr, zc, outf, first, have_up, compute, kc, kk);
+                } else {
+                    const NbrShfl<NV, LX, V, decltype(edgeld)> nbr{edgeld, xl};
+                    march_level_core<NV, V>(st, rowld, nbr, zc, outf, first, have_up, compute, kc, kk);
                 }
-                Epilogue<T, MODE>::template storevec<NC>(o0, o1, o2,
-                                                         row_off + (long long)half * g.pj + (long long)kk * g.pk, a,
-                                                         b, d, g, j + half, i0);
-            };
-            auto out = [&](const V (&ru)[NC], const V (&rv)[NC], const V (&rw)[NC], const V (&u0)[NC],
-                           const V (&v0)[NC], const V (&w0)[NC]) {
-                if (kk < kb) return;
-                if (valid) out_row(ru, rv, rw, u0, v0, w0, 0);
-                if (RP == 2 && valid2) out_row(ru, rv, rw, u0, v0, w0, 1);
-            };
-            march_level<NC, LX>(st, rowld, edgeld, out, xl, lp == 0, have_up, (kk >= kb) && (kk >= 2), kc, kk,
-                                nzp2);
+            } else {
+                march_level<NV, LX>(st, rowld, edgeld, out, xl, first, have_up, compute, kc, kk, nzp2);
+            }
         }
 #if PW_MARCH_SPLIT_ARRIVE
         // this warp is done with the plane of level kk; the last warp to say
@@ -741,14 +1050,23 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
 #endif
     };
 
-    // One level per loop iteration.  (Two or three per iteration, so that the
-    // carried rows rotate by register renaming instead of moves, cost
-    // registers and CTAs per SM and measured 15-25 % slower on GB300; reloading
-    // the level's rows from the staged plane instead of carrying them gained
-    // nothing either.)
-    bool aborted = false;
-    for (int kk = pb; kk <= ke && !aborted; ++kk)
-        if (!level(kk)) aborted = true;
+    // The tile's first level (rows loaded, maybe only priming), then the
+    // steady levels, then the top level of the grid if the tile reaches it.
+    // Steady levels kk > pb always compute (kk >= kb, kk >= 2) and, below the
+    // top, always have level kk+1.  The x-pair form takes two steady levels
+    // per iteration (PW_MARCH_UNROLL_XP), so the carried rows change places
+    // by register renaming rather than moves.
+    using Fast = std::integral_constant<bool, PW_MARCH_FAST != 0>;
+    using Gen = std::integral_constant<bool, false>;
+    bool aborted = !level(pb, Gen{});
+    int kk = pb + 1;
+    const int kfast = (ke == nz) ? ke - 1 : ke;
+    constexpr int kUnroll = XP ? PW_MARCH_UNROLL_XP : PW_MARCH_UNROLL;
+#pragma unroll kUnroll
+    for (; kk <= kfast && !aborted; ++kk)
+        if (!level(kk, Fast{})) aborted = true;
+    for (; kk <= ke && !aborted; ++kk)
+        if (!level(kk, Gen{})) aborted = true;
 
 #if PW_MARCH_SPLIT_ARRIVE
     // every warp has left the march (each wait is bounded): the ring is free
@@ -773,50 +1091,54 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP>
             if (!mbar_wait_bounded(&bars[slot(p)], parity(p), kDrainLimitNs)) break;
     }
 #endif
+    (void)tbase;
     return !aborted;
 }
 
 // One grid, one tile per CTA: blockIdx = (tile column, tile row, k segment).
-template <typename T, int LX, int TY, int S, int MODE, int NC, int RP>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP>::THREADS,
-                                  (tma_min_blocks<T, LX, TY, S, NC, RP>()))
+template <typename T, int LX, int TY, int S, int MODE, int NC, int RP, int XP>
+__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
+                                  (tma_min_blocks<T, LX, TY, S, NC, RP, XP>()))
     tma_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
                const __grid_constant__ CUtensorMap tm_w, T* __restrict__ o0, T* __restrict__ o1,
                T* __restrict__ o2, const GridDev g, const int ox, const int nseg, const int seg0, const FoldedCoef kc,
                const float dt, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MarchSmem<T, LX, TY, S, NC, RP> sm(smem_raw);
+    MarchSmem<T, LX, TY, S, NC, RP, XP> sm(smem_raw);
     const int bz = seg0 + blockIdx.z;
     const int kb = 1 + (int)(((long long)bz * g.nz) / nseg);
     const int ke = (int)(((long long)(bz + 1) * g.nz) / nseg);
     if (ke < kb) return;   // empty k segment (the host never launches one)
     sm.init(threadIdx.y * 32 + threadIdx.x);
     uint32_t ring = 0;
-    march_tile<T, LX, TY, S, MODE, NC, RP>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, kc, dt,
-                                                   blockIdx.x, blockIdx.y, kb, ke, ring, err);
+    march_tile<T, LX, TY, S, MODE, NC, RP, XP>(sm, &tm_u, &tm_v, &tm_w, o0, o1, o2, g, ox, kc, dt, blockIdx.x,
+                                               blockIdx.y, kb, ke, ring, err);
 }
 
 // Instantiated single-grid launch shapes: (lanes per row, rows, stages, cells
-// per thread along x, rows per thread).  8 cells per thread and the packed
-// two-row form are instantiated for 16-bit storage only (8 cells: one
-// 16-byte shared-memory access per row vector; two rows: the 16-bit values
-// unpack straight into row pairs, where FP32 rows would need register moves).
-#define PW_TMA_CONFIGS(X) X(32, 4, 4, 4, 1) X(32, 8, 3, 4, 1) X(32, 8, 4, 4, 1) X(32, 8, 6, 4, 1) \
-    X(32, 16, 3, 4, 1) X(16, 4, 4, 4, 1) X(16, 8, 4, 4, 1) X(16, 4, 4, 8, 1) X(16, 8, 4, 8, 1)        \
-    X(32, 8, 4, 4, 2) X(32, 16, 4, 4, 2) X(16, 8, 4, 4, 2)
+// per thread along x, rows per thread, x pairs).  8 cells per thread, the
+// packed two-row form and the x-pair form are instantiated for 16-bit
+// storage only (8 cells: one 16-byte shared-memory access per row vector; two
+// rows and x pairs: the 16-bit values unpack straight into FP32x2 operands,
+// where FP32 rows would need register moves).
+#define PW_TMA_CONFIGS(X) X(32, 4, 4, 4, 1, 0) X(32, 8, 3, 4, 1, 0) X(32, 8, 4, 4, 1, 0) X(32, 8, 6, 4, 1, 0) \
+    X(32, 16, 3, 4, 1, 0) X(16, 4, 4, 4, 1, 0) X(16, 8, 4, 4, 1, 0) X(16, 4, 4, 8, 1, 0) X(16, 8, 4, 8, 1, 0)   \
+    X(32, 8, 4, 4, 2, 0) X(32, 16, 4, 4, 2, 0) X(16, 8, 4, 4, 2, 0)                                            \
+    X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1) X(16, 16, 4, 8, 1, 1) X(32, 4, 4, 4, 1, 1) X(32, 8, 4, 4, 1, 1)   \
+    X(16, 8, 4, 4, 1, 1)
 
-template <typename T, int NC, int RP>
-constexpr bool nc_ok() { return (NC == 4 && RP == 1) || sizeof(T) == 2; }
+template <typename T, int NC, int RP, int XP = 0>
+constexpr bool nc_ok() { return (NC == 4 && RP == 1 && XP == 0) || sizeof(T) == 2; }
 
-template <typename T, int LX, int TY, int S, int MODE, int NC, int RP>
+template <typename T, int LX, int TY, int S, int MODE, int NC, int RP, int XP>
 static cudaError_t launch_tma_inst(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1,
                                    void* o2, const Scales& sc, const CoefDev& cf, float dt, int* err, int nseg,
                                    int seg0, int seg_count, cudaStream_t s) {
-  if constexpr (!nc_ok<T, NC, RP>()) {
+  if constexpr (!nc_ok<T, NC, RP, XP>()) {
     return cudaErrorInvalidConfiguration;
   } else {
-    using L = TmaLayout<T, LX, TY, S, NC, RP>;
-    auto kern = tma_kernel<T, LX, TY, S, MODE, NC, RP>;
+    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
+    auto kern = tma_kernel<T, LX, TY, S, MODE, NC, RP, XP>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
     if (seg_count <= 0) seg_count = nseg - seg0;
@@ -832,10 +1154,10 @@ template <typename T, int MODE>
 static cudaError_t launch_tma_mode(const GridDev& g, int ox, const CUtensorMap* maps, void* o0, void* o1, void* o2,
                                    const Scales& sc, const CoefDev& cf, float dt, int* err,
                                    const TmaConfig& c, cudaStream_t s) {
-#define PW_DISPATCH(LX_, TY_, S_, NC_, RP_)                                                                   \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_)                           \
-        return launch_tma_inst<T, LX_, TY_, S_, MODE, NC_, RP_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, c.nseg, \
-                                                                c.seg0, c.seg_count, s);
+#define PW_DISPATCH(LX_, TY_, S_, NC_, RP_, XP_)                                                        \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_)      \
+        return launch_tma_inst<T, LX_, TY_, S_, MODE, NC_, RP_, XP_>(g, ox, maps, o0, o1, o2, sc, cf, dt, err, \
+                                                                     c.nseg, c.seg0, c.seg_count, s);
     PW_TMA_CONFIGS(PW_DISPATCH)
 #undef PW_DISPATCH
     return cudaErrorInvalidConfiguration;

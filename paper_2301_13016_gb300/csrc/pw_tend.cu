@@ -33,9 +33,9 @@ cudaError_t launch_tend_tma(pw_dtype_t dt, const GridDev& g, int ox, const CUten
 }
 
 bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c) {
-#define PW_SUP(LX_, TY_, S_, NC_, RP_)                                              \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_) \
-        return (NC_ == 4 && RP_ == 1) || dtype_size(dt) == 2;
+#define PW_SUP(LX_, TY_, S_, NC_, RP_, XP_)                                                       \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_) \
+        return (NC_ == 4 && RP_ == 1 && XP_ == 0) || dtype_size(dt) == 2;
     PW_TMA_CONFIGS(PW_SUP)
 #undef PW_SUP
     return false;
@@ -43,9 +43,10 @@ bool tma_config_supported(pw_dtype_t dt, const TmaConfig& c) {
 
 template <typename T>
 static size_t smem_t(const TmaConfig& c) {
-#define PW_SM(LX_, TY_, S_, NC_, RP_)                                               \
-    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_) \
-        return TmaLayout<T, LX_, TY_, S_, NC_, RP_>::SMEM;
+#define PW_SM(LX_, TY_, S_, NC_, RP_, XP_)                                                            \
+    if constexpr (nc_ok<T, NC_, RP_, XP_>())                                                           \
+        if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_) \
+            return TmaLayout<T, LX_, TY_, S_, NC_, RP_, XP_>::SMEM;
     PW_TMA_CONFIGS(PW_SM)
 #undef PW_SM
     return 0;
@@ -63,11 +64,11 @@ size_t tma_smem_bytes(pw_dtype_t dt, const TmaConfig& c) {
 template <typename T>
 static int blocks_per_sm_t(const TmaConfig& c) {
     int n = 0;
-#define PW_OCC(LX_, TY_, S_, NC_, RP_)                                                                 \
-    if constexpr (nc_ok<T, NC_, RP_>())                                                                \
-        if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_) {              \
-            auto kern = tma_kernel<T, LX_, TY_, S_, MODE_TEND, NC_, RP_>;                              \
-            using L = TmaLayout<T, LX_, TY_, S_, NC_, RP_>;                                            \
+#define PW_OCC(LX_, TY_, S_, NC_, RP_, XP_)                                                           \
+    if constexpr (nc_ok<T, NC_, RP_, XP_>())                                                           \
+        if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_) { \
+            auto kern = tma_kernel<T, LX_, TY_, S_, MODE_TEND, NC_, RP_, XP_>;                         \
+            using L = TmaLayout<T, LX_, TY_, S_, NC_, RP_, XP_>;                                       \
             if (set_smem_attr_once(kern, (int)L::SMEM) != cudaSuccess) return 0;                       \
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, L::THREADS, L::SMEM) != cudaSuccess) \
                 return 0;                                                                              \

@@ -72,7 +72,7 @@ SIGNATURES = [
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
     ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
                                        ctypes.POINTER(_VP)]),
-    ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
+    ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
     ("pw_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(_I32)]),
     ("pw_batch_tendencies", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -244,7 +244,9 @@ class PW:
 
     def set_tma_config(self, ty=0, stages=0, nseg=0, lanes_x=0, cells=0, rows=0):
         """Launch shape of the k-march kernel (0 = automatic); rows = rows per
-        thread (2: packed FP32x2 arithmetic on row pairs, 16-bit storage)."""
+        thread (2: packed FP32x2 arithmetic on row pairs, 16-bit storage;
+        3: one row per thread, its cells packed as FP32x2 pairs along x,
+        16-bit storage)."""
         _check(lib().pw_set_tma_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(nseg),
                                        int(rows)), "pw_set_tma_config")
 
@@ -428,11 +430,13 @@ class Batch:
         except Exception:
             pass
 
-    def set_config(self, lanes_x=0, ty=0, stages=0, ctas_per_sm=0, rows=0):
+    def set_config(self, lanes_x=0, ty=0, stages=0, ctas_per_sm=0, rows=0, cells=0):
         """Tile shape of the batched kernel (0 = default field); rows = rows
-        per thread (2: packed FP32x2 on row pairs, 16-bit storage)."""
-        _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(ty), int(stages), int(ctas_per_sm), int(rows)),
-               "pw_batch_set_config")
+        per thread (2: packed FP32x2 on row pairs; 3: one row, its cells
+        packed as FP32x2 pairs along x; both 16-bit storage); cells = cells
+        per thread along x (4, or 8 with x pairs when every nx allows)."""
+        _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(ctas_per_sm),
+                                         int(rows)), "pw_batch_set_config")
 
     def info(self):
         ni, cells, ctas = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()

@@ -82,19 +82,25 @@ def test_batch_graph_replay_and_pointer_change():
             assert torch.allclose(x, y, rtol=0, atol=0, equal_nan=True)
 
 
+PACKED = [(32, 8, 4, 4, 2), (16, 8, 4, 4, 2), (32, 8, 4, 4, 3), (16, 8, 4, 4, 3), (16, 8, 4, 8, 3),
+          (16, 4, 4, 8, 3)]
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-@pytest.mark.parametrize("cfg", [(32, 8, 4), (16, 8, 4)])
+@pytest.mark.parametrize("cfg", PACKED, ids=["x".join(map(str, p)) for p in PACKED])
 def test_batch_two_rows_per_thread_equals_single_grid(dtype, cfg):
-    """16-bit batches with two rows per thread (packed FP32x2) give the bits of
-    the single-grid kernel in the same shape, grid by grid; FP32 batches
-    reject that shape."""
+    """16-bit batches in the packed FP32x2 forms (two rows per thread, or one
+    row with its cells paired along x) give the bits of the single-grid kernel
+    in the same shape, grid by grid (with 8 cells per thread also on grids
+    whose nx is 4 mod 8: the last vector of a row stores 4 cells); FP32
+    batches reject those shapes."""
+    lx, ty, st, cells, rows = cfg
     b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES, dtype=dtype)
-    lx, ty, st = cfg
-    b.set_config(lanes_x=lx, ty=ty, stages=st, rows=2)
+    b.set_config(lanes_x=lx, ty=ty, stages=st, rows=rows, cells=cells)
     _run(b, dev, outs)
     for g, c, d, o in zip(grids, coeffs, dev, outs):
         h = pwlib.PW(g, c)
-        h.set_tma_config(ty, st, 1, lanes_x=lx, cells=4, rows=2)
+        h.set_tma_config(ty, st, 1, lanes_x=lx, cells=cells, rows=rows)
         single = [g.alloc(fill=NAN) for _ in range(3)]
         h.tendencies(*d, *single)
         h.sync()
@@ -102,7 +108,7 @@ def test_batch_two_rows_per_thread_equals_single_grid(dtype, cfg):
             assert torch.equal(x.view(torch.int16), y.view(torch.int16))
     b32, *_ = _make_batch(SHAPES[:2])
     with pytest.raises(pwlib.PwError) as e:
-        b32.set_config(lanes_x=32, ty=8, stages=4, rows=2)
+        b32.set_config(lanes_x=lx, ty=ty, stages=st, rows=rows, cells=cells)
     assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
 
 

@@ -125,20 +125,42 @@ def test_eight_cells_per_thread(dtype, ty, nseg):
         floor = 2 * precision.MIN_NORMAL[dtype] / so
         assert np.all(np.abs(interior(x) - interior(r)) <= us * np.abs(interior(r)) + 2.0 ** -19 * interior(at) + floor)
         assert np.all(np.abs(interior(x) - interior(y)) <= 2 * us * np.abs(interior(r)) + 2.0 ** -18 * interior(at) + 2 * floor)
-    with pytest.raises(pwlib.PwError):
-        pwlib.PW(pwlib.Grid(132, 8, 4, dtype=dtype), inputs.make_coeffs(4)).set_tma_config(4, 4, 0, lanes_x=16, cells=8)
+    # nx = 132 = 4 mod 8: source terms with 8 cells per thread (the row's last
+    # vector stores 4 cells) equal the 4-cell kernel's bits; fused steps need
+    # nx to be a multiple of 8
+    g2 = pwlib.Grid(132, 8, 4, dtype=dtype)
+    f2 = inputs.random_fields(132, 8, 4)
+    h2 = pwlib.PW(g2, inputs.make_coeffs(4))
+    d2 = [g2.from_dense(x, scale=s) for x, s in zip(f2, sc[:3])]
+    got = {}
+    for cells in (4, 8):
+        h2.set_tma_config(4, 4, 0, lanes_x=16, cells=cells)
+        o2 = [g2.alloc(fill=NAN) for _ in range(3)]
+        h2.tendencies(*d2, *o2, scale=sc)
+        h2.sync()
+        got[cells] = [t.view(torch.int16).clone() for t in o2]
+    for a_, b_ in zip(got[4], got[8]):
+        assert torch.equal(a_, b_)
+    with pytest.raises(pwlib.PwError) as e:
+        h2.step(*d2, *[g2.alloc() for _ in range(3)], 1.0, 1, scale=sc[:3])
+    assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
 
 
-PAIRED = [(32, 8, 4, 4, 2), (32, 16, 4, 4, 2), (16, 8, 4, 4, 2)]
+# (lanes, rows, stages, cells, form): form 2 = two rows per thread (each cell
+# paired with the cell below it), 3 = one row per thread with its cells paired
+# along x (cell q with cell q + cells/2)
+PAIRED = [(32, 8, 4, 4, 2), (32, 16, 4, 4, 2), (16, 8, 4, 4, 2),
+          (16, 4, 4, 8, 3), (16, 8, 4, 8, 3), (16, 16, 4, 8, 3), (32, 4, 4, 4, 3), (32, 8, 4, 4, 3)]
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 @pytest.mark.parametrize("cfg", PAIRED, ids=["x".join(map(str, p)) for p in PAIRED])
 def test_two_rows_per_thread_bitwise(dtype, cfg):
-    """Two rows per thread (packed FP32x2 arithmetic on row pairs) gives the
-    same bits as one row per thread, for the source terms and for fused steps,
-    on tiles ragged in x (264 = 2 x 128 + 8 columns) and in y (13 rows: the
-    last row pair has its second row outside the grid)."""
+    """The packed FP32x2 forms (two rows per thread, or the cells of one row
+    paired along x) give the same bits as one scalar row per thread, for the
+    source terms and for fused steps, on tiles ragged in x (264 = 2 x 128 + 8
+    columns) and in y (13 rows: the last row pair has its second row outside
+    the grid)."""
     nx, ny, nz = 264, 13, 10
     c = inputs.make_coeffs(nz)
     f = inputs.random_fields(nx, ny, nz)

@@ -353,6 +353,39 @@ def test_host_path_async_calls_back_to_back(shape):
             assert np.array_equal(interior(x), interior(g.to_dense(t).numpy()))
 
 
+@pytest.mark.parametrize("shape,kinds", [((36, 8, 5), (0, 0, 0, 0)), ((256, 20, 16), (1, 0, 1, 0))],
+                         ids=["unpipelined", "generic_then_pipelined"])
+def test_host_path_async_calls_on_different_streams(shape, kinds):
+    """Asynchronous host calls on one handle, each on its own stream, without
+    waiting in between: the one-launch path (nz < 8, or the generic kernel)
+    runs on the caller's stream only, so each call must still be ordered after
+    the previous one (they share the staging buffers).  Kinds alternate the
+    generic one-launch path with the pipelined TMA path on the same handle.
+    Every output equals the oracle for its own inputs."""
+    nx, ny, nz = shape
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, c)
+    sets = []
+    for n, kind in enumerate(kinds):
+        seed = 31 + n
+        dense = inputs.random_fields(nx, ny, nz, seeds=(seed, seed + 10, seed + 20))
+        ref = oracle.tendencies(*[x.numpy() for x in dense], c)
+        hin = [g.from_dense(x, device="cpu").pin_memory() for x in dense]
+        hout = [torch.full((g.alloc_elems,), 7.0, dtype=torch.float32).pin_memory() for _ in range(3)]
+        sets.append((kind, ref, hin, hout, torch.cuda.Stream()))
+    for kind, _, hin, hout, s in sets:
+        h.set_kernel(kind)
+        h.tendencies_host_async(*hin, *hout, stream=s)
+    for *_, s in sets:
+        h.sync(s)
+    torch.cuda.synchronize()
+    for kind, ref, hin, hout, s in sets:
+        got = [g.to_dense(t).numpy() for t in hout]
+        for e in rel_errs(got, ref):
+            assert e <= 1e-5
+
+
 def test_binding_rejects_tensors_on_the_wrong_side():
     """Host tensors never reach a device entry point (the GPU would fault on
     the address) and device tensors never reach the host entry point."""

@@ -10,6 +10,7 @@ stopping at its first failure has run every other test before it.
 """
 import numpy as np
 import pytest
+import torch
 
 import paper_2301_13016_gb300 as pwlib
 from paper_2301_13016_gb300 import inputs
@@ -60,3 +61,36 @@ def test_noalloc_dot_other_grid_and_limit():
         h2.weighted_dot_noalloc(t, t, wk=np.ones(nz + 2))
     assert e.value.status == pwlib.PW_ERR_UNSUPPORTED
     assert "4096" in str(e.value)
+
+
+def test_noalloc_first_call_leaves_free_memory_unchanged():
+    """The property the entry point exists for: on a fresh handle, its first
+    call leaves the device's free memory exactly as it was, while the
+    allocating pw_weighted_dot's first call on a fresh handle takes its
+    scratch from the device (here 2.4 MB, so at least one new 2 MiB page)."""
+    c, g, h0, dev, outs = _fields(128, 16, 12, 31)
+    wk = c.dz_u
+    # the library's device code, the static array with it, is loaded by the
+    # first call in the process; measure from the second handle on
+    ref = h0.weighted_dot_noalloc(dev[0], outs[0], wk=wk, k0=2, k1=g.nz)
+    torch.cuda.synchronize()
+    h1 = pwlib.PW(g, c)
+    free0 = torch.cuda.mem_get_info()[0]
+    got = h1.weighted_dot_noalloc(dev[0], outs[0], wk=wk, k0=2, k1=g.nz)
+    again = h1.weighted_dot_noalloc(dev[0], outs[0], wk=wk, k0=2, k1=g.nz)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert got == ref and again == ref
+
+    # positive control: the same measurement sees the allocating entry point's
+    # scratch (4 * (blocks + 1) + nz + 2 doubles; nz = 300000 makes it 2.4 MB)
+    nz = 300_000
+    gd = pwlib.Grid(4, 4, nz, pitch_j=8, pitch_k=48, origin=9)
+    hd = pwlib.PW(gd, inputs.make_coeffs(nz))
+    t = gd.alloc(fill=1.0)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    val = hd.weighted_dot(t, t)
+    torch.cuda.synchronize()
+    assert free1 - torch.cuda.mem_get_info()[0] >= 2 * 1024 * 1024
+    assert val == pytest.approx(4 * 4 * nz, rel=1e-12)
