@@ -136,22 +136,27 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
  * Launch shape of the TMA k-march kernel: lanes_x = lanes per row, cells =
  * consecutive cells per thread along x (tile width lanes_x * cells columns),
  * ty = rows per CTA, stages = planes buffered per CTA, nseg = CTAs along z
- * (0 = chosen from the grid and SM count), rows_per_thread = 1, or 2 (a
- * thread computes each cell together with the cell one row further on, in
- * packed FP32x2 arithmetic; same results bit for bit).  A shape given here is
- * used for every call, its zero fields at (lanes_x, ty, stages, cells,
- * rows_per_thread) = (32, 4, 4, 4, 1); all zero restores the automatic
- * choice, which depends on the call: (32, 4, 4, 4, 1) for FP32;
- * (32, 8, 4, 4, 2) for the source terms with 16-bit storage; (16, 8, 4, 8, 1)
- * for fused steps with 16-bit storage when nx is a multiple of 8 (else
- * (32, 4, 4, 4, 1)); (16, 4, 4, 4, 1) when nx <= 64; nseg the count that
- * best fills the last wave of CTAs per plane marched (segments of >= 2
- * levels; more segments only for a >= 3 % gain).  Instantiated (lanes_x,
- * ty, stages, cells, rows_per_thread): (32,4,4,4,1) (32,8,3,4,1) (32,8,4,4,1)
- * (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1) (16,8,4,4,1), and for 16-bit
- * storage also (16,4,4,8,1) (16,8,4,8,1) (32,8,4,4,2) (32,16,4,4,2)
- * (16,8,4,4,2); others, and cells = 8 with nx not a multiple of 8, give
- * PW_ERR_UNSUPPORTED.
+ * (0 = chosen from the grid and SM count), rows_per_thread = how a thread
+ * holds its cells: 1 = one row, scalar FP32 arithmetic; 2 = the same cells in
+ * two rows, each cell paired with the cell one row further on in packed
+ * FP32x2 arithmetic; 3 = one row, its cells packed as FP32x2 pairs along x
+ * (cell q with cell q + cells/2); every form gives the same results bit for
+ * bit.  A shape given here is used for every call, its zero fields at
+ * (lanes_x, ty, stages, cells, rows_per_thread) = (32, 4, 4, 4, 1); all zero
+ * restores the automatic choice, which depends on the call: (32, 4, 4, 4, 1)
+ * for FP32; (16, 8, 4, 8, 3) for 16-bit storage (fused steps: when nx is a
+ * multiple of 8, else (32, 4, 4, 4, 3)); (16, 4, 4, 4, 1) when nx <= 64; nseg
+ * the count that best fills the last wave of CTAs per plane marched
+ * (segments of >= 2 levels; more segments only for a >= 3 % gain).
+ * Instantiated (lanes_x, ty, stages, cells, rows_per_thread): (32,4,4,4,1)
+ * (32,8,3,4,1) (32,8,4,4,1) (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1)
+ * (16,8,4,4,1), and for 16-bit storage also (16,4,4,8,1) (16,8,4,8,1)
+ * (32,8,4,4,2) (32,16,4,4,2) (16,8,4,4,2) (16,4,4,8,3) (16,8,4,8,3)
+ * (16,16,4,8,3) (32,4,4,4,3) (32,8,4,4,3) (16,8,4,4,3); others give
+ * PW_ERR_UNSUPPORTED.  With cells = 8 the source terms accept any nx that is
+ * a multiple of 4 (a row's last vector may hold 4 cells of the grid); fused
+ * steps then need nx to be a multiple of 8 (else PW_ERR_UNSUPPORTED at the
+ * step call).
  */
 pw_status_t pw_set_tma_config(pw_handle_t h, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
                               int32_t nseg, int32_t rows_per_thread);
@@ -398,7 +403,7 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t
  * packed as FP32x2 pairs along x; 2 and 3 for 16-bit storage only; all give
  * the same bits) from the instantiated set (lanes_x, ty, stages, cells,
  * rows_per_thread) (32,4,4,4,1) (32,8,4,4,1) (16,4,4,4,1) (16,8,4,4,1)
- * (32,8,4,4,2) (16,8,4,4,2) (32,4,4,4,3) (32,8,4,4,3) (16,4,4,4,3)
+ * (16,16,4,4,1) (32,8,4,4,2) (16,8,4,4,2) (32,4,4,4,3) (32,8,4,4,3) (16,4,4,4,3)
  * (16,8,4,4,3) (16,4,4,8,3) (16,8,4,8,3), zero fields at (32, 4, 4, 4, 1);
  * others, and cells = 8 with a grid whose nx is not a multiple of 8, give
  * PW_ERR_UNSUPPORTED.  ctas_per_sm = resident CTAs per SM of the persistent

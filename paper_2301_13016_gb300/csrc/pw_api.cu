@@ -248,12 +248,12 @@ static pw_status_t check_device_ptrs(pw_handle_t h, const void* const* ps, int n
 // stages, one row per thread).  Otherwise the shape measured fastest on GB300
 // (2048^2 x 64):
 //   FP32:                       32 lanes x 4 cells x 4 rows (HBM-bound);
-//   16-bit, source terms:       32 lanes x 4 cells x 8 rows, two rows per
-//                               thread in packed FP32x2 (BF16 327, FP16 332
-//                               Gcell/s with the scales folded; one row per
-//                               thread: 305, 296);
-//   16-bit, steps (nx % 8 = 0): 16 lanes x 8 cells x 8 rows (BF16 279, FP16
-//                               267 Gcell-steps/s; two rows: 266, 247);
+//   16-bit (source terms; steps when nx % 8 = 0):
+//                               16 lanes x 8 cells x 8 rows, each thread's
+//                               cells packed as FP32x2 pairs along x (BF16
+//                               401, FP16 400 Gcell/s; two rows per thread
+//                               315, 331);
+//   16-bit steps, nx % 8 = 4:   32 lanes x 4 cells x 4 rows in x pairs;
 //   nx <= 64:                   16 lanes x 4 cells x 4 rows;
 // 4 stages, and the k segments chosen below.
 static TmaConfig choose_tma(pw_handle_t h, bool step) {
@@ -281,13 +281,13 @@ static TmaConfig choose_tma(pw_handle_t h, bool step) {
         c.rp = 1;
         if (gr.nx <= 64) {
             c.lx = 16;
-        } else if (half && !step) {
-            c.ty = 8;
-            c.rp = 2;
-        } else if (half && step && gr.nx % 8 == 0) {
-            c.lx = 16;
+        } else if (half && (!step || gr.nx % 8 == 0)) {
+            c.lx = 16;   // x pairs of 8 cells: tiles of 128 columns
             c.nc = 8;
             c.ty = 8;
+            c.xp = 1;
+        } else if (half) {
+            c.xp = 1;    // x pairs of 4 cells
         }
     }
     if (u.nseg) {

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
 // Instantiated tile shapes (lanes per row, rows, stages, cells per thread,
 // rows per thread, x pairs); the packed forms for 16-bit storage only.
 #define PW_BATCH_CONFIGS(X) X(32, 4, 4, 4, 1, 0) X(32, 8, 4, 4, 1, 0) X(16, 4, 4, 4, 1, 0) X(16, 8, 4, 4, 1, 0) \
+    X(16, 16, 4, 4, 1, 0) \
     X(32, 8, 4, 4, 2, 0) X(16, 8, 4, 4, 2, 0) X(32, 4, 4, 4, 1, 1) X(32, 8, 4, 4, 1, 1) X(16, 4, 4, 4, 1, 1)      \
     X(16, 8, 4, 4, 1, 1) X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1)
 

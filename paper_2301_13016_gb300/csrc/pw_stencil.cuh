@@ -661,6 +661,10 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 #ifndef PW_MARCH_FAST
 #define PW_MARCH_FAST 1
 #endif
+// x-pair form: one CTA barrier per pair of steady levels instead of per level.
+#ifndef PW_MARCH_PAIR_SYNC
+#define PW_MARCH_PAIR_SYNC 1
+#endif
 // x-pair form: staged rows read through explicit 32-bit shared addresses
 // (with two levels per iteration: BF16 384 against 376 Gcell/s at 2048^2 x 64).
 #ifndef PW_MARCH_LDS_ASM
@@ -945,8 +949,9 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
     // neither the tile's first nor the top of the grid (its rows come from the
     // last level, it computes, and level kk+1 exists), with those facts
     // compile-time constants.
-    auto level = [&](const int kk, auto fast) -> bool {
+    auto level = [&](const int kk, auto fast, auto sync) -> bool {
         constexpr bool FAST = decltype(fast)::value;
+        constexpr bool SYNC = decltype(sync)::value;   // end the level with the CTA barrier
         lp = kk - pb;
         if constexpr (L::CTAB) {
             if (lp > 0 && lp % L::CTAB_LEVELS == 0) {
@@ -1039,14 +1044,22 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
         }
         return !*abort_flag;
 #else
-        __syncthreads();
-        if (*abort_flag) return false;
-        if (tid == 0 && issued < np) {
-            fence_proxy_async_smem();
-            issue(issued);   // plane lp + S into the slot level kk just released
-            ++issued;
+        if constexpr (!SYNC) {
+            return true;   // the planes of level kk are released at the next barrier
+        } else {
+            __syncthreads();
+            if (*abort_flag) return false;
+            // every plane up to lp is free: refill the slots of those not yet
+            // refilled (one after a level with its own barrier, two after a
+            // pair of levels)
+            if (tid == 0) {
+                for (; issued < np && issued <= lp + S; ++issued) {
+                    fence_proxy_async_smem();
+                    issue(issued);   // plane `issued` into the slot of plane issued - S
+                }
+            }
+            return true;
         }
-        return true;
 #endif
     };
 
@@ -1056,17 +1069,26 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
     // top, always have level kk+1.  The x-pair form takes two steady levels
     // per iteration (PW_MARCH_UNROLL_XP), so the carried rows change places
     // by register renaming rather than moves.
+    // With PW_MARCH_PAIR_SYNC the x-pair form's two levels of an iteration
+    // share one CTA barrier: after the second, the planes of both are free.
     using Fast = std::integral_constant<bool, PW_MARCH_FAST != 0>;
     using Gen = std::integral_constant<bool, false>;
-    bool aborted = !level(pb, Gen{});
+    using Sync = std::integral_constant<bool, true>;
+    using NoSync = std::integral_constant<bool, false>;   // (ignored with PW_MARCH_SPLIT_ARRIVE)
+    bool aborted = !level(pb, Gen{}, Sync{});
     int kk = pb + 1;
     const int kfast = (ke == nz) ? ke - 1 : ke;
-    constexpr int kUnroll = XP ? PW_MARCH_UNROLL_XP : PW_MARCH_UNROLL;
+    if constexpr (XP && PW_MARCH_PAIR_SYNC) {
+        for (; kk + 1 <= kfast && !aborted; kk += 2)
+            if (!level(kk, Fast{}, NoSync{}) || !level(kk + 1, Fast{}, Sync{})) aborted = true;
+    } else {
+        constexpr int kUnroll = XP ? PW_MARCH_UNROLL_XP : PW_MARCH_UNROLL;
 #pragma unroll kUnroll
-    for (; kk <= kfast && !aborted; ++kk)
-        if (!level(kk, Fast{})) aborted = true;
+        for (; kk <= kfast && !aborted; ++kk)
+            if (!level(kk, Fast{}, Sync{})) aborted = true;
+    }
     for (; kk <= ke && !aborted; ++kk)
-        if (!level(kk, Gen{})) aborted = true;
+        if (!level(kk, Gen{}, Sync{})) aborted = true;
 
 #if PW_MARCH_SPLIT_ARRIVE
     // every warp has left the march (each wait is bounded): the ring is free

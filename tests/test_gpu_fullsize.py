@@ -2,9 +2,9 @@
 times, where the plain FP32 full-size check (test_gpu_tendencies) does not
 reach:
 
-  * 16-bit storage at 2048 x 2048 x 64 (automatic shape: two rows per thread,
-    packed FP32x2) on sampled 32 x 32-column boxes, against the per-cell
-    kernel and total bounds of the 16-bit tests;
+  * 16-bit storage at 2048 x 2048 x 64 (automatic shape: 8 cells per
+    thread packed as FP32x2 pairs along x) on sampled 32 x 32-column boxes,
+    against the per-cell kernel and total bounds of the 16-bit tests;
   * the 512-grid batch (1.77 G cells) in the autotuner's tile, 8 sampled grids
     (largest and smallest among them) checked whole against the FP64 oracle;
   * the periodic adjoint at 512 x 512 x 64 (the rollout's grid) through the
@@ -45,7 +45,7 @@ def test_16bit_sampled_parity_2048(dtype):
     sc = precision.suggest_scales([float(x.abs().max()) for x in f], c, dtype)
     g = pwlib.Grid(nx, ny, nz, dtype=dtype)
     h = pwlib.PW(g, c)
-    assert h.tma_config()["rows"] == 2
+    assert h.tma_config()["rows"] == 3 and h.tma_config()["cells"] == 8   # the benchmark's 16-bit shape
     dev = [g.from_dense(x, scale=s) for x, s in zip(f, sc[:3])]
     outs = [g.alloc(fill=NAN) for _ in range(3)]
     h.tendencies(*dev, *outs, scale=sc)

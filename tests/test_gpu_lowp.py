@@ -192,11 +192,11 @@ def test_two_rows_per_thread_needs_16bit_storage():
 
 def test_automatic_launch_shapes():
     """The automatic k-march shape per call: FP32 32 lanes x 4 cells x 4 rows;
-    16-bit source terms 32 x 4 x 8 with two rows per thread; 16-bit steps
-    16 x 8 x 8 (nx a multiple of 8, else the FP32 shape); 16 x 4 x 4 for
-    grids at most 64 columns wide, with k segments of 2 levels; a shape set
-    by pw_set_tma_config is used as given (zero fields at the scalar
-    defaults) for every call."""
+    16-bit source terms 16 x 8 x 8 with the cells paired along x (rows = 3);
+    16-bit steps the same when nx is a multiple of 8, else 32 x 4 x 4 in x
+    pairs; 16 x 4 x 4 for grids at most 64 columns wide, with k segments of
+    2 levels; a shape set by pw_set_tma_config is used as given (zero fields
+    at the scalar defaults) for every call."""
     c = inputs.make_coeffs(8)
 
     def pick(g, step=False):
@@ -206,10 +206,11 @@ def test_automatic_launch_shapes():
     for step in (False, True):
         assert pick(pwlib.Grid(256, 64, 8), step) == f32
     for dtype in ("bf16", "f16"):
+        xp8 = dict(lanes_x=16, cells=8, ty=8, stages=4, rows=3)
         for nx in (256, 260):
-            assert pick(pwlib.Grid(nx, 64, 8, dtype=dtype)) == dict(lanes_x=32, cells=4, ty=8, stages=4, rows=2)
-        assert pick(pwlib.Grid(256, 64, 8, dtype=dtype), True) == dict(lanes_x=16, cells=8, ty=8, stages=4, rows=1)
-        assert pick(pwlib.Grid(260, 64, 8, dtype=dtype), True) == f32
+            assert pick(pwlib.Grid(nx, 64, 8, dtype=dtype)) == xp8
+        assert pick(pwlib.Grid(256, 64, 8, dtype=dtype), True) == xp8
+        assert pick(pwlib.Grid(260, 64, 8, dtype=dtype), True) == dict(f32, rows=3)
     for dtype in ("f32", "bf16"):
         for step in (False, True):
             assert pwlib.PW(pwlib.Grid(64, 64, 8, dtype=dtype), c).tma_config(step) == dict(
