@@ -167,6 +167,23 @@ def source_version():
     return {"git_sha": git_sha, "source_sha256": h.hexdigest()[:16]}
 
 
+def host_numa():
+    """NUMA nodes of the host and the node nvidia-smi and sysfs give for GPU 0
+    (where pinned host buffers should sit for the host link)."""
+    out = {"nodes": None, "gpu_node": None}
+    try:
+        out["nodes"] = len([d for d in os.listdir("/sys/devices/system/node") if re.fullmatch(r"node\d+", d)])
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", "0"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/numa_node"
+        with open(path) as fh:
+            out["gpu_node"] = int(fh.read().strip())
+    except Exception:
+        pass
+    return out
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the TMA kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
@@ -449,7 +466,7 @@ def run_ours(args, rank, world, local):
            "api": "pw_tendencies_host_async, steps back to back, one sync",
            "one_call_at_a_time": whole_job_rate(cells * args.e2e_steps, world, sync_s) / 1e9,
            "h2d_bytes_per_step": 3 * 4 * (nx + 2) * (ny + 2) * nz, "d2h_bytes_per_step": 3 * 4 * cells,
-           "steps": args.e2e_steps}
+           "steps": args.e2e_steps, "host_numa": host_numa()}
 
     if rank != 0:
         return

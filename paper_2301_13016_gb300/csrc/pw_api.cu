@@ -358,6 +358,11 @@ cudaError_t set_smem_attr_once_impl(const void* kern, int bytes) {
     for (auto& d : done)
         if (d.first == kern && d.second == dev) return cudaSuccess;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // all the shared memory an SM has, so that shared memory does not hold the
+    // resident CTAs below what the registers allow (the kernels stage their
+    // data in shared memory and barely use the L1 cache)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) done.emplace_back(kern, dev);
     return e;
 }

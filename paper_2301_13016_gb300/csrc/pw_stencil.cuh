@@ -405,10 +405,21 @@ __device__ __forceinline__ void zcoef_fill(float4* tab, const FoldedCoef& k, con
 // are live at once.  Pair sums along x are shared by neighbouring cells.
 // Every form of the k-march runs this one sequence of operations, so they
 // agree bit for bit.
-template <int NC, typename V, class Row, class Nbr, class ZC, class Out>
+//
+// pdx(f, p, store): where the lower flux products live between levels: a
+// no-op when they stay in st's registers (PdRegs), else a copy of field f's
+// products from (store = false) or to (store = true) shared memory, done just
+// before their use and just after they are formed.
+struct PdRegs {
+    template <class A>
+    __device__ __forceinline__ void operator()(int, A&, bool) const {}
+};
+
+template <int NC, typename V, class Row, class Nbr, class ZC, class Out, class Pd = PdRegs>
 __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row& row, const Nbr& nbr, const ZC& zc,
                                                  const Out& out, const bool first, const bool have_up,
-                                                 const bool compute, const FoldedCoef& k, const int kk) {
+                                                 const bool compute, const FoldedCoef& k, const int kk,
+                                                 const Pd& pdx = Pd{}) {
     using O = VOps<V>;
     if (first) {
         row(F_U, 0, 0, st.u0);
@@ -470,6 +481,8 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
                 pys[c] = O::add(VS[c], VS[c + 1]);       // v(j-1,i) + v(j-1,i+1)
             }
 #pragma unroll
+            pdx(F_U, st.pdu, false);
+#pragma unroll
             for (int c = 0; c < NC; ++c) {
                 V x = O::mul(kxu, O::fma(O::neg(U[c + 2]), pxu[c + 1], O::mul(U[c], pxu[c])));
                 x = O::fma(kyu, O::fma(O::neg(un[c]), pxv[c], O::mul(us[c], pys[c])), x);
@@ -480,6 +493,7 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
         out(F_U, r, st.u0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) st.pdu[c] = O::mul(st.u0[c], pzu_n[c]);   // u(k) * (w(k,i) + w(k,i+1))
+        pdx(F_U, st.pdu, true);
 
         // ---- sv
         V wn[NC];
@@ -497,6 +511,7 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
             for (int c = 0; c < NC; ++c) UN[c + 1] = un[c];
 #pragma unroll
             for (int c = 0; c < NC + 1; ++c) qx[c] = O::add(U[c], UN[c]);   // u(j,i-1) + u(j+1,i-1)
+            pdx(F_V, st.pdv, false);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 V y = O::mul(kxv, O::fma(O::neg(Vv[c + 2]), qx[c + 1], O::mul(Vv[c], qx[c])));
@@ -511,6 +526,7 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
         out(F_V, r, st.v0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) st.pdv[c] = O::mul(st.v0[c], pzv_n[c]);   // v(k) * (w(k,j) + w(k,j+1))
+        pdx(F_V, st.pdv, true);
 
         // ---- sw (zero at the lid)
         if (have_up) {
@@ -532,6 +548,7 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
             for (int c = 0; c < NC; ++c) UU[c + 1] = uu[c];
 #pragma unroll
             for (int c = 0; c < NC + 1; ++c) rx[c] = O::add(U[c], UU[c]);   // u(k,i-1) + u(k+1,i-1)
+            pdx(F_W, st.pdw, false);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 V z = O::mul(kxw, O::fma(O::neg(W[c + 2]), rx[c + 1], O::mul(W[c], rx[c])));
@@ -544,6 +561,7 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
         out(F_W, r, st.w0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) st.pdw[c] = O::mul(st.w0[c], pzw_n[c]);   // w(k) * (w(k) + w(k+1))
+        pdx(F_W, st.pdw, true);
     } else {
         // no source terms at this level: zeros out, and the rows and flux
         // products of level kk+1
@@ -565,6 +583,9 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
             st.pdv[c] = O::mul(st.v0[c], O::add(st.w0[c], wn[c]));
             st.pdw[c] = O::mul(st.w0[c], O::add(st.w0[c], wu[c]));
         }
+        pdx(F_U, st.pdu, true);
+        pdx(F_V, st.pdv, true);
+        pdx(F_W, st.pdw, true);
     }
 
     // roll: level kk+1 becomes level kk
@@ -665,6 +686,18 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 #ifndef PW_MARCH_PAIR_SYNC
 #define PW_MARCH_PAIR_SYNC 1
 #endif
+// x-pair form: the lower flux products kept in shared memory between levels
+// (fewer registers a thread) instead of registers.
+// (BF16 378 -> 386, FP16 374 -> 382 Gcell/s at 2048^2 x 64: 128 registers,
+// four CTAs per SM instead of three)
+#ifndef PW_MARCH_PD_SMEM
+#define PW_MARCH_PD_SMEM 1
+#endif
+// Register target of the x-pair shapes with 8 cells a thread and the flux
+// products in shared memory (128: four CTAs of 4 warps per SM, no spills).
+#ifndef PW_TMA_REGS_XP
+#define PW_TMA_REGS_XP 128
+#endif
 // x-pair form: staged rows read through explicit 32-bit shared addresses
 // (with two levels per iteration: BF16 384 against 376 Gcell/s at 2048^2 x 64).
 #ifndef PW_MARCH_LDS_ASM
@@ -692,7 +725,11 @@ struct TmaLayout {
     static constexpr int CTAB_LEVELS = 128;
     static constexpr size_t CTAB_OFF =
         (((size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16 + 4 * S + 15) / 16) * 16;
-    static constexpr size_t SMEM = CTAB_OFF + (CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0);
+    // x-pair form with PW_MARCH_PD_SMEM: the lower flux products of every
+    // thread (3 fields x NC/2 pairs) in shared memory between levels
+    static constexpr bool PD_SMEM = XP == 1 && PW_MARCH_PD_SMEM;
+    static constexpr size_t PD_OFF = CTAB_OFF + (CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0);
+    static constexpr size_t SMEM = PD_OFF + (PD_SMEM ? (size_t)3 * (NC / 2) * THREADS * sizeof(float2) : 0);
     static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
     static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
     static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
@@ -712,7 +749,9 @@ constexpr int tma_min_blocks() {
     using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
     constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
     constexpr int by_threads = 2048 / L::THREADS;
-    constexpr int by_regs = NC * RP == 8 ? 65536 / (L::THREADS * PW_TMA_REGS8) : PW_TMA_MAX_MINB;
+    constexpr int by_regs = (L::PD_SMEM && NC == 8)
+                                ? 65536 / (L::THREADS * PW_TMA_REGS_XP)
+                                : (NC * RP == 8 ? 65536 / (L::THREADS * PW_TMA_REGS8) : PW_TMA_MAX_MINB);
     constexpr int m0 = by_smem < by_threads ? by_smem : by_threads;
     constexpr int m = m0 < by_regs ? m0 : by_regs;
     return m < 1 ? 1 : m;
@@ -728,7 +767,9 @@ struct MarchSmem {
     volatile int* flag;   // [0] abort, [1] work item broadcast, [2] planes issued (highest + 1)
     uint32_t* cnt;        // warps done with each slot's plane
     float4* ctab;         // vertical coefficient table (L::CTAB)
+    float4* pd;           // lower flux products (L::PD_SMEM)
     __device__ __forceinline__ MarchSmem(unsigned char* raw) {
+        pd = reinterpret_cast<float4*>(raw + L::PD_OFF);
         stages = reinterpret_cast<T*>(raw);
         bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * L::STAGE * sizeof(T));
         flag = reinterpret_cast<volatile int*>(bars + S);
@@ -1015,7 +1056,24 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
             const bool first = !FAST && lp == 0, compute = FAST || ((kk >= kb) && (kk >= 2));
             if constexpr (L::CTAB) {
                 const ZCoefTab zc{sm.ctab, tbase};
-                if constexpr (XP) {
+                if constexpr (XP && L::PD_SMEM) {
+                    // thread tid's pairs 2m, 2m+1 of field f at float4 (f*NV/2 + m)*THREADS + tid
+                    auto pdx = [&](int f, V (&p)[NV], bool store) {
+#pragma unroll
+                        for (int m = 0; m < NV / 2; ++m) {
+                            float4* a = sm.pd + (f * (NV / 2) + m) * L::THREADS + tid;
+                            if (store) {
+                                *a = make_float4(p[2 * m].x, p[2 * m].y, p[2 * m + 1].x, p[2 * m + 1].y);
+                            } else {
+                                const float4 t = *a;
+                                p[2 * m] = make_float2(t.x, t.y);
+                                p[2 * m + 1] = make_float2(t.z, t.w);
+                            }
+                        }
+                    };
+                    const NbrPairs<NV, decltype(nbrld)> nbr{nbrld};
+                    march_level_core<NV, V>(st, rowld, nbr, zc, outf, first, have_up, compute, kc, kk, pdx);
+                } else if constexpr (XP) {
                     const NbrPairs<NV, decltype(nbrld)> nbr{nbrld};
                     march_level_core<NV, V>(st, rowld, nbr, zc, outf, first, have_up, compute, kc, kk);
                 } else {
