@@ -152,7 +152,8 @@ pw_status_t pw_set_kernel(pw_handle_t h, int32_t kind);
  * (32,8,3,4,1) (32,8,4,4,1) (32,8,6,4,1) (32,16,3,4,1) (16,4,4,4,1)
  * (16,8,4,4,1), and for 16-bit storage also (16,4,4,8,1) (16,8,4,8,1)
  * (32,8,4,4,2) (32,16,4,4,2) (16,8,4,4,2) (16,4,4,8,3) (16,8,4,8,3)
- * (16,16,4,8,3) (32,4,4,4,3) (32,8,4,4,3) (16,8,4,4,3); others give
+ * (16,16,4,8,3) (32,4,4,4,3) (32,8,4,4,3) (16,8,4,4,3) (8,8,4,8,3)
+ * (8,16,4,8,3); others give
  * PW_ERR_UNSUPPORTED.  With cells = 8 the source terms accept any nx that is
  * a multiple of 4 (a row's last vector may hold 4 cells of the grid); fused
  * steps then need nx to be a multiple of 8 (else PW_ERR_UNSUPPORTED at the
@@ -397,14 +398,15 @@ typedef struct pw_batch_s *pw_batch_t;
 pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t *coeffs,
                             pw_batch_t *out);
 
-/* Tile shape of the batched kernel: lanes_x (32 or 16), cells (per thread
+/* Tile shape of the batched kernel: lanes_x (32, 16 or 8), cells (per thread
  * along x: 4, or 8), ty, stages, rows_per_thread (1; 2: a cell and the one a
  * row further on in packed FP32x2 arithmetic; 3: one row whose cells are
  * packed as FP32x2 pairs along x; 2 and 3 for 16-bit storage only; all give
  * the same bits) from the instantiated set (lanes_x, ty, stages, cells,
  * rows_per_thread) (32,4,4,4,1) (32,8,4,4,1) (16,4,4,4,1) (16,8,4,4,1)
  * (16,16,4,4,1) (32,8,4,4,2) (16,8,4,4,2) (32,4,4,4,3) (32,8,4,4,3) (16,4,4,4,3)
- * (16,8,4,4,3) (16,4,4,8,3) (16,8,4,8,3), zero fields at (32, 4, 4, 4, 1);
+ * (16,8,4,4,3) (16,4,4,8,3) (16,8,4,8,3) (8,8,4,8,3) (8,16,4,8,3)
+ * (8,16,4,4,1) (32,16,4,4,1), zero fields at (32, 4, 4, 4, 1);
  * others, and cells = 8 with a grid whose nx is not a multiple of 8, give
  * PW_ERR_UNSUPPORTED.  ctas_per_sm = resident CTAs per SM of the persistent
  * launch (0 = as many as fit).  Rebuilds the work list; the next call

@@ -19,13 +19,15 @@ import torch
 BATCH_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=4, ctas_per_sm=c, rows=rp, cells=nc)
                     for lx, ty, nc, rp in ((32, 4, 4, 1), (32, 8, 4, 1), (16, 4, 4, 1), (16, 8, 4, 1), (16, 16, 4, 1),
                                            (32, 8, 4, 2),
-                                           (16, 8, 4, 2), (32, 8, 4, 3), (16, 8, 4, 3), (16, 8, 8, 3), (16, 4, 8, 3))
+                                           (16, 8, 4, 2), (32, 8, 4, 3), (16, 8, 4, 3), (16, 8, 8, 3), (16, 4, 8, 3),
+                                           (8, 8, 8, 3), (8, 16, 8, 3), (8, 16, 4, 1), (32, 16, 4, 1))
                     for c in (0, 2)]
 GRID_CANDIDATES = [dict(lanes_x=lx, ty=ty, stages=st, nseg=ns, cells=nc, rows=rp)
                    for lx, ty, st, nc, rp in ((32, 4, 4, 4, 1), (32, 8, 4, 4, 1), (32, 8, 6, 4, 1), (16, 4, 4, 4, 1),
                                               (16, 8, 4, 4, 1), (16, 4, 4, 8, 1), (16, 8, 4, 8, 1), (32, 8, 4, 4, 2),
                                               (32, 16, 4, 4, 2), (16, 8, 4, 4, 2), (16, 4, 4, 8, 3),
-                                              (16, 8, 4, 8, 3), (16, 16, 4, 8, 3), (32, 4, 4, 4, 3), (32, 8, 4, 4, 3))
+                                              (16, 8, 4, 8, 3), (16, 16, 4, 8, 3), (32, 4, 4, 4, 3), (32, 8, 4, 4, 3),
+                                              (8, 8, 4, 8, 3), (8, 16, 4, 8, 3))
                    for ns in (0, 1, 2, 4)]
 
 

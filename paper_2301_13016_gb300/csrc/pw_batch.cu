@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
 #define PW_BATCH_CONFIGS(X) X(32, 4, 4, 4, 1, 0) X(32, 8, 4, 4, 1, 0) X(16, 4, 4, 4, 1, 0) X(16, 8, 4, 4, 1, 0) \
     X(16, 16, 4, 4, 1, 0) \
     X(32, 8, 4, 4, 2, 0) X(16, 8, 4, 4, 2, 0) X(32, 4, 4, 4, 1, 1) X(32, 8, 4, 4, 1, 1) X(16, 4, 4, 4, 1, 1)      \
-    X(16, 8, 4, 4, 1, 1) X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1)
+    X(16, 8, 4, 4, 1, 1) X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1) X(8, 8, 4, 8, 1, 1) X(8, 16, 4, 8, 1, 1)        \
+    X(8, 16, 4, 4, 1, 0) X(32, 16, 4, 4, 1, 0)
 
 template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
 static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,

@@ -67,11 +67,10 @@ struct StepImages {
             if (dxm) put(o + dym + dxm);
         }
     }
-    // a vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
+    // one field's vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
     template <typename T, int N>
-    static __device__ __forceinline__ void vec(T* o0, T* o1, T* o2, long long o, const float (&a)[N],
-                                               const float (&b)[N], const float (&c)[N], const GridDev& g, int j,
-                                               int i0) {
+    static __device__ __forceinline__ void vec1(T* of, long long o, const float (&a)[N], const GridDev& g, int j,
+                                                int i0) {
         const int H = g.halo;
         const bool west = (i0 <= H), east = (i0 + N - 1 > g.nx - H);
         const long long dyp = (j <= H) ? (long long)g.ny * g.pj : 0;
@@ -82,21 +81,12 @@ struct StepImages {
         for (int s = 0; s < 3; ++s) {
             if (s > 0 && shifts[s] == 0) continue;
             const long long p = o + shifts[s];
-            if (s > 0) {   // the row image
-                storev<N>(o0 + p, a);
-                storev<N>(o1 + p, b);
-                storev<N>(o2 + p, c);
-            }
+            if (s > 0) storev<N>(of + p, a);   // the row image
 #pragma unroll
             for (int q = 0; q < N; ++q) {
                 const int i = i0 + q;
-                auto put = [&](long long x) {
-                    o0[x] = Store<T>::from_f(a[q]);
-                    o1[x] = Store<T>::from_f(b[q]);
-                    o2[x] = Store<T>::from_f(c[q]);
-                };
-                if (west && i <= H) put(p + q + g.nx);           // i -> i + nx
-                if (east && i > g.nx - H) put(p + q - g.nx);     // i -> i - nx
+                if (west && i <= H) of[p + q + g.nx] = Store<T>::from_f(a[q]);       // i -> i + nx
+                if (east && i > g.nx - H) of[p + q - g.nx] = Store<T>::from_f(a[q]); // i -> i - nx
             }
         }
     }
@@ -630,8 +620,8 @@ __device__ __forceinline__ void march_level(MarchRegs<NC, V>& st, const Row& row
 // ahead of the level being computed, so every input element is read from HBM
 // once and the copy engine, not the warps, keeps bytes in flight.
 //
-// LX lanes cover one row (LX = 32: one warp per row; LX = 16: two rows per
-// warp, for narrow grids).  A thread computes NC consecutive cells along x,
+// LX lanes cover one row (LX = 32: one warp per row; LX = 16 or 8: two or
+// four rows per warp, for narrow tiles).  A thread computes NC consecutive cells along x,
 // in one row (RP = 1) or in two adjacent rows (RP = 2: a cell and the cell
 // below it form one float2, and the arithmetic runs on the packed FP32x2
 // instructions, half the instructions for the same operations).
@@ -730,7 +720,7 @@ struct TmaLayout {
     static constexpr bool PD_SMEM = XP == 1 && PW_MARCH_PD_SMEM;
     static constexpr size_t PD_OFF = CTAB_OFF + (CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0);
     static constexpr size_t SMEM = PD_OFF + (PD_SMEM ? (size_t)3 * (NC / 2) * THREADS * sizeof(float2) : 0);
-    static_assert(LX == 32 || LX == 16, "LX must be 16 or 32");
+    static_assert(LX == 32 || LX == 16 || LX == 8, "LX must be 8, 16 or 32");
     static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
     static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
     static_assert(TY % (RPW * RP) == 0, "TY must be a multiple of the rows per warp");
@@ -1205,7 +1195,8 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
     X(32, 16, 3, 4, 1, 0) X(16, 4, 4, 4, 1, 0) X(16, 8, 4, 4, 1, 0) X(16, 4, 4, 8, 1, 0) X(16, 8, 4, 8, 1, 0)   \
     X(32, 8, 4, 4, 2, 0) X(32, 16, 4, 4, 2, 0) X(16, 8, 4, 4, 2, 0)                                            \
     X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1) X(16, 16, 4, 8, 1, 1) X(32, 4, 4, 4, 1, 1) X(32, 8, 4, 4, 1, 1)   \
-    X(16, 8, 4, 4, 1, 1)
+    X(16, 8, 4, 4, 1, 1) X(8, 8, 4, 8, 1, 1) X(8, 16, 4, 8, 1, 1) X(8, 16, 4, 4, 1, 0) X(32, 16, 4, 4, 1, 0)      \
+    X(16, 16, 4, 4, 1, 0)
 
 template <typename T, int NC, int RP, int XP = 0>
 constexpr bool nc_ok() { return (NC == 4 && RP == 1 && XP == 0) || sizeof(T) == 2; }

@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                 storev<NC>(o0 + o, a);
                 storev<NC>(o1 + o, b);
                 storev<NC>(o2 + o, d);
-                StepImages::vec<T, NC>(o0, o1, o2, o, a, b, d, g, j, i0);
+                StepImages::vec1<T, NC>(o0, o, a, g, j, i0);
+                StepImages::vec1<T, NC>(o1, o, b, g, j, i0);
+                StepImages::vec1<T, NC>(o2, o, d, g, j, i0);
             };
             march_level<NC, 32>(st2, rowld2, edgeld2, out2, lane, m == kb1, m + 1 <= ke1, (m >= kb) && (m >= 2), kc,
                                 m, nzp2);

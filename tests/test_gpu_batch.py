@@ -39,7 +39,7 @@ def _run(b, dev, outs, scale=None):
 SHAPES = [(32, 40, 8), (384, 36, 5), (100, 17, 12), (64, 64, 3), (260, 9, 20), (36, 300, 6), (128, 4, 4)]
 
 
-@pytest.mark.parametrize("cfg", [(32, 4, 4), (32, 8, 4), (16, 4, 4), (16, 8, 4)])
+@pytest.mark.parametrize("cfg", [(32, 4, 4), (32, 8, 4), (16, 4, 4), (16, 8, 4), (16, 16, 4), (8, 16, 4), (32, 16, 4)])
 def test_batch_matches_oracle_and_single_grid(cfg):
     b, grids, coeffs, fields, dev, outs = _make_batch(SHAPES)
     lx, ty, st = cfg
@@ -83,7 +83,7 @@ def test_batch_graph_replay_and_pointer_change():
 
 
 PACKED = [(32, 8, 4, 4, 2), (16, 8, 4, 4, 2), (32, 8, 4, 4, 3), (16, 8, 4, 4, 3), (16, 8, 4, 8, 3),
-          (16, 4, 4, 8, 3)]
+          (16, 4, 4, 8, 3), (8, 8, 4, 8, 3), (8, 16, 4, 8, 3)]
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])

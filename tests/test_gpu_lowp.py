@@ -150,7 +150,8 @@ def test_eight_cells_per_thread(dtype, ty, nseg):
 # paired with the cell below it), 3 = one row per thread with its cells paired
 # along x (cell q with cell q + cells/2)
 PAIRED = [(32, 8, 4, 4, 2), (32, 16, 4, 4, 2), (16, 8, 4, 4, 2),
-          (16, 4, 4, 8, 3), (16, 8, 4, 8, 3), (16, 16, 4, 8, 3), (32, 4, 4, 4, 3), (32, 8, 4, 4, 3)]
+          (16, 4, 4, 8, 3), (16, 8, 4, 8, 3), (16, 16, 4, 8, 3), (32, 4, 4, 4, 3), (32, 8, 4, 4, 3),
+          (16, 8, 4, 4, 3), (8, 8, 4, 8, 3), (8, 16, 4, 8, 3)]
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
