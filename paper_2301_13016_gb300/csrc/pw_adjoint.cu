@@ -18,6 +18,8 @@
 // periodic (C ranges over the interior; output cells wrap around the doubly
 // periodic domain, which equals the full-array result folded back onto the
 // interior; u, v, w must carry periodic halos).
+#include <algorithm>
+
 #include "pw_device.cuh"
 
 #include <type_traits>
@@ -182,7 +184,12 @@ struct AdjLayout {
     static constexpr int STAGE = 6 * FIELD;
     static constexpr uint32_t TX_BYTES = 6u * FIELD_RAW * 4u;
     // the ring, one mbarrier per slot, 4 flag words, one release counter per slot
-    static constexpr size_t SMEM = (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16 + 4 * S;
+    // the vertical coefficients {tzc1, tzc2, tzd1, tzd2} of levels kb-1..ke+1
+    // of the CTA's k segment, one float4 per level (the host keeps a segment
+    // within CTZ_LEVELS - 2 levels)
+    static constexpr int CTZ_LEVELS = 256;
+    static constexpr size_t CTZ_OFF = (((size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16 + 4 * S + 15) / 16) * 16;
+    static constexpr size_t SMEM = CTZ_OFF + (size_t)CTZ_LEVELS * sizeof(float4);
 };
 
 struct AdjMaps {
@@ -283,6 +290,12 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
         abort_flag[0] = 0;
         fence_mbar_init();
     }
+    float4* const ctz = reinterpret_cast<float4*>(smem_raw + L::CTZ_OFF);   // entry k - (kb-1): level k
+    for (int e = tid; e <= ke - kb + 2; e += 32 * TY) {
+        const int k = kb - 1 + e;
+        ctz[e] = make_float4(__ldg(cf.tz + k), __ldg(cf.tz + nzp2 + k), __ldg(cf.tz + 2 * nzp2 + k),
+                             __ldg(cf.tz + 3 * nzp2 + k));
+    }
     __syncthreads();
     if (tid == 0) {
         for (int f = 0; f < 6; ++f) prefetch_tensormap(&maps.m[f]);
@@ -290,10 +303,6 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
         abort_flag[1] = issued;
     }
 
-    const float* tzc1 = cf.tz;
-    const float* tzc2 = cf.tz + nzp2;
-    const float* tzd1 = cf.tz + 2 * nzp2;
-    const float* tzd2 = cf.tz + 3 * nzp2;
     const float tcx = cf.tcx, tcy = cf.tcy;
     const int r = ty + 1;
     const int c0 = kAdjPAD + NA * lane;
@@ -387,9 +396,10 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
             // (loading these here, after the level's rows, measured 3-5 % faster
             // on GB300 than loading them before the plane wait or one level ahead)
             const bool has_m = (K - 1 >= 1), has_p = (K + 1 <= nz);
-            const float c1p = has_p ? tzc1[K + 1] : 0.f, c2m = has_m ? tzc2[K - 1] : 0.f, c2 = tzc2[K];
-            const float d1p = has_p ? tzd1[K + 1] : 0.f, d1 = tzd1[K], d2 = tzd2[K];
-            const float d2m = has_m ? tzd2[K - 1] : 0.f;
+            const float4 zm = ctz[K - kb], z0 = ctz[K - kb + 1], zp = ctz[K - kb + 2];   // levels K-1, K, K+1
+            const float c1p = has_p ? zp.x : 0.f, c2m = has_m ? zm.y : 0.f, c2 = z0.y;
+            const float d1p = has_p ? zp.z : 0.f, d1 = z0.z, d2 = z0.w;
+            const float d2m = has_m ? zm.w : 0.f;
             float ru[NA], rv[NA], rw[NA];
 
             // the gather of one level; EDGE: levels where some terms do not exist
@@ -619,6 +629,7 @@ static cudaError_t launch_adj_inst(const GridDev& g, int ox, const AdjMaps& m, f
     auto kern = adjoint_vec_kernel<NA, TY, S>;
     cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
     if (e != cudaSuccess) return e;
+    nseg = std::max(nseg, (g.nz + L::CTZ_LEVELS - 3) / (L::CTZ_LEVELS - 2));   // segments within the table
     dim3 grid((g.nx + L::TX - 1) / L::TX, (g.ny + TY - 1) / TY, nseg);
     kern<<<grid, dim3(32, TY), L::SMEM, s>>>(m, gu, gv, gw, g, ox, nseg, cf, alpha, accumulate, add_lambda, err);
     return cudaGetLastError();

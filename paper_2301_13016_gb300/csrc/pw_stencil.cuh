@@ -782,17 +782,19 @@ struct MarchSmem {
 
 // The thread's NC consecutive 16-bit values at p (aligned to NC elements) as
 // NC/2 FP32 pairs (value q, value q + NC/2): the pairing of the x-pair form.
+// (FP16: the conversion selects the half of the word itself; BF16: the half
+// is moved into the upper 16 bits of an FP32 word, which is exact)
 template <typename T>
 __device__ __forceinline__ float lo_f(uint32_t w) {
     if constexpr (std::is_same<T, __half>::value)
-        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+        return __low2float(*reinterpret_cast<const __half2*>(&w));
     else
         return __uint_as_float(w << 16);
 }
 template <typename T>
 __device__ __forceinline__ float hi_f(uint32_t w) {
     if constexpr (std::is_same<T, __half>::value)
-        return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+        return __high2float(*reinterpret_cast<const __half2*>(&w));
     else
         return __uint_as_float(w & 0xffff0000u);
 }
