@@ -1125,9 +1125,11 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
     using Gen = std::integral_constant<bool, false>;
     using Sync = std::integral_constant<bool, true>;
     using NoSync = std::integral_constant<bool, false>;   // (ignored with PW_MARCH_SPLIT_ARRIVE)
+    // (One loop holding one general and one steady-pair body, smaller code,
+    // measured slower: BF16 380 against 382, steps 322 against 345.)
+    const int kfast = (ke == nz) ? ke - 1 : ke;
     bool aborted = !level(pb, Gen{}, Sync{});
     int kk = pb + 1;
-    const int kfast = (ke == nz) ? ke - 1 : ke;
     if constexpr (XP && PW_MARCH_PAIR_SYNC) {
         for (; kk + 1 <= kfast && !aborted; kk += 2)
             if (!level(kk, Fast{}, NoSync{}) || !level(kk + 1, Fast{}, Sync{})) aborted = true;
