@@ -192,19 +192,16 @@ static pw_status_t encode_map(pw_handle_t h, const void* ptr, int lx, int ty, CU
     return encode_map_box(h, ptr, tma_box_width(h->grid.dtype, lx, nc), ty + 2, out);
 }
 
-pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int lx, int ty, CUtensorMap* out, int nc) {
-    return encode_tensor_map_box(g, ptr, tma_box_width(g.dtype, lx, nc), ty + 2, out);
+pw_status_t pw::encode_tensor_map(const pw_grid_t& g, const void* ptr, int lx, int ty, CUtensorMap* out, int nc,
+                                  int l2_promotion) {
+    return encode_tensor_map_box(g, ptr, tma_box_width(g.dtype, lx, nc), ty + 2, out, l2_promotion);
 }
-
-// L2 promotion of the TMA loads (build knob): 0 none, 1 64 B, 2 128 B, 3 256 B.
-#ifndef PW_TMA_L2_PROMOTION
-#define PW_TMA_L2_PROMOTION 3
-#endif
 
 // 3D map of one field: x = the padded row from its first element (element
 // i = 0 at x = ox), y = rows from j = 1-halo, z = levels 0..nz+1.  Boxes of
 // box_w x box_h x 1; out-of-range elements read as zero.
-pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out) {
+pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int box_w, int box_h, CUtensorMap* out,
+                                      int l2_promotion) {
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     int ox = 0;
@@ -220,7 +217,7 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
     cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(out, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, (CUtensorMapL2promotion)PW_TMA_L2_PROMOTION,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, (CUtensorMapL2promotion)l2_promotion,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
     return PW_OK;

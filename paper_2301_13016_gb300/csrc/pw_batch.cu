@@ -406,7 +406,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
             const pw_grid_t& g = b->grids[q];
             for (int a = 0; a < 3; ++a) {
                 pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->cfg.lx, b->cfg.ty,
-                                                   &b->h_maps[3 * (size_t)q + a], b->cfg.nc);
+                                                   &b->h_maps[3 * (size_t)q + a], b->cfg.nc, PW_BATCH_L2_PROMOTION);
                 if (st != PW_OK) return st;
             }
             BatchGridDev& r = b->h_grids[q];
