@@ -681,7 +681,8 @@ def form_batch(args, dtype="f32"):
     _form_line(args, name, f"PW tendencies Gcell/s, {n} independent grids in one persistent graph-replayed launch",
                val, "Gcell/s", {"workload": f"{n} grids, nx, ny ~ U{{32..384 step 4}}, nz ~ U{{32..128}} (seed 2304), "
                                             f"{dtype.upper()} storage, FP32 math, random 10*N(0,1)",
-                                "cells": info["cells"], "items": info["items"], "ctas": info["ctas"], "tile": cfg},
+                                "cells": info["cells"], "items": info["items"], "ctas": info["ctas"], "tile": cfg,
+                                "narrow_last_columns": b.narrow_shape()},
                {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
                 "autotune_s": tune_s, "autotune_ms": times,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

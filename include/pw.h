@@ -407,13 +407,29 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t *grids, const pw_coeffs_t
  * (16,16,4,4,1) (32,8,4,4,2) (16,8,4,4,2) (32,4,4,4,3) (32,8,4,4,3) (16,4,4,4,3)
  * (16,8,4,4,3) (16,4,4,8,3) (16,8,4,8,3) (8,8,4,8,3) (8,16,4,8,3)
  * (8,16,4,4,1) (32,16,4,4,1), zero fields at (32, 4, 4, 4, 1);
- * others, and cells = 8 with a grid whose nx is not a multiple of 8, give
- * PW_ERR_UNSUPPORTED.  ctas_per_sm = resident CTAs per SM of the persistent
+ * others give PW_ERR_UNSUPPORTED (cells = 8 takes grids with nx = 4 mod 8:
+ * the row's last vector is computed whole and its grid cells stored).  ctas_per_sm = resident CTAs per SM of the persistent
  * launch (0 = as many as fit).  Rebuilds the work list; the next call
  * captures a new graph.  The autotuner (paper_2301_13016_gb300.autotune)
  * chooses these by measurement. */
 pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t cells, int32_t ty, int32_t stages,
                                 int32_t ctas_per_sm, int32_t rows_per_thread);
+
+/* Narrow last columns (enable = 1, the default, or 0).  With the tile shapes
+ * (lanes_x, ty, stages, cells, rows_per_thread) (16,16,4,4,1) (16,8,4,4,1)
+ * (32,8,4,4,1) for FP32 storage and (8,16,4,8,3) (16,8,4,8,3) for 16-bit
+ * storage, a grid whose last column of tiles would hold at most half a tile
+ * of cells marches that column with tiles half as wide and of the same
+ * thread count: (8,32,4,4,1) (8,16,4,4,1) (16,16,4,4,1), resp. (8,16,4,4,3)
+ * (8,16,4,8,3).  The recipe of uneven grids (widths 32..384 in steps of 4)
+ * then computes 1.10 x its cells instead of 1.17 x with 64 x 16 tiles.  The
+ * results are the same bits either way (one per-cell operation sequence).
+ * Other shapes ignore the setting.  Rebuilds the work list. */
+pw_status_t pw_batch_set_narrow_columns(pw_batch_t b, int32_t enable);
+
+/* The narrow shape in use (lanes_x, cells, ty; all 0 when the current shape
+ * has none or narrow columns are off; any output pointer may be NULL). */
+pw_status_t pw_batch_narrow_shape(pw_batch_t b, int32_t *lanes_x, int32_t *cells, int32_t *ty);
 
 /* Work items, interior cells and persistent CTAs of the current shape (any
  * output pointer may be NULL). */

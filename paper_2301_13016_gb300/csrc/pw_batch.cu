@@ -22,10 +22,33 @@ namespace pw {
 
 struct BatchGridDev {
     GridDev g;
-    int ox, tiles_x, tiles_y, nseg;
+    int ox;
+    int tiles_x, tiles_y;   // the grid's wide tiles (columns, rows)
+    int ntiles_y, nbx;      // narrow last column: its tiles (0: none) and its index in narrow tiles
+    int nseg;
     float tcx, tcy;
     const float* tz;
     void* o[3];
+};
+
+// The tile shapes of a batched kernel: a wide one (LX, TY, NC) and,
+// optionally (NC2 > 0), a narrow one of half its width and the same thread
+// count (LX2, TY2, NC2) for a grid's last column when that column holds at
+// most half a wide tile.  Both march through one plane ring whose mbarriers
+// sit after the larger shape's ring region.
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP, int LX2, int TY2, int NC2>
+struct BatchShapes {
+    static constexpr bool DUAL = NC2 > 0;
+    using LW = TmaLayout<T, LX, TY, S, NC, RP, XP>;
+    using LN = TmaLayout<T, DUAL ? LX2 : LX, DUAL ? TY2 : TY, S, DUAL ? NC2 : NC, RP, XP>;
+    static constexpr size_t RING = LW::RING_BYTES > LN::RING_BYTES ? LW::RING_BYTES : LN::RING_BYTES;
+    static constexpr size_t SMEM =
+        LW::smem_bytes(RING) > LN::smem_bytes(RING) ? LW::smem_bytes(RING) : LN::smem_bytes(RING);
+    static constexpr int THREADS = LW::THREADS;
+    static constexpr int MAPS = DUAL ? 6 : 3;   // tensor maps per grid (u, v, w per shape)
+    static_assert(!DUAL || LN::THREADS == LW::THREADS, "both shapes use every thread of the CTA");
+    static_assert(!DUAL || 2 * LN::TX == LW::TX, "the narrow shape is half as wide");
+    static_assert(LN::CTAB == LW::CTAB, "one coefficient-table layout");
 };
 
 // Resident CTAs per SM the batch kernel's register budget is sized for (at
@@ -35,11 +58,11 @@ struct BatchGridDev {
 #ifndef PW_BATCH_MINB
 #define PW_BATCH_MINB 0
 #endif
-template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP, int LX2, int TY2, int NC2>
 constexpr int batch_min_blocks() {
-    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
-    constexpr int by_smem = (int)((227u * 1024u) / L::SMEM);
-    constexpr int by_threads = 2048 / L::THREADS;
+    using B = BatchShapes<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>;
+    constexpr int by_smem = (int)((227u * 1024u) / B::SMEM);
+    constexpr int by_threads = 2048 / B::THREADS;
     constexpr int m = by_smem < by_threads ? by_smem : by_threads;
     constexpr int want = PW_BATCH_MINB ? PW_BATCH_MINB : tma_min_blocks<T, LX, TY, S, NC, RP, XP>();
     return want < m ? want : m;
@@ -47,15 +70,17 @@ constexpr int batch_min_blocks() {
 
 // NC cells per thread along x; RP = 2: two rows per thread in packed FP32x2
 // arithmetic; XP = 1: the cells of one row packed as FP32x2 pairs (16-bit
-// storage for both).
-template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
-__global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
-                                  (batch_min_blocks<T, LX, TY, S, NC, RP, XP>()))
+// storage for both).  NC2 > 0: a grid's narrow last column runs with the
+// (LX2, TY2, NC2) tiles.
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP, int LX2, int TY2, int NC2>
+__global__ void __launch_bounds__((BatchShapes<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>::THREADS),
+                                  (batch_min_blocks<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>()))
     tma_batch_kernel(const BatchGridDev* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                      const int2* __restrict__ items, const int n_items, int* __restrict__ counter, const Scales sc,
                      int* __restrict__ err) {
+    using B = BatchShapes<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MarchSmem<T, LX, TY, S, NC, RP, XP> sm(smem_raw);
+    MarchSmem<T, LX, TY, S, NC, RP, XP> sm(smem_raw, B::RING);
     const int tid = threadIdx.y * 32 + threadIdx.x;
     sm.init(tid);
     uint32_t ring = 0;
@@ -67,19 +92,32 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
         if (it >= n_items) break;
         const int2 item = items[it];
         const BatchGridDev& bg = grids[item.x];
-        const int per_seg = bg.tiles_x * bg.tiles_y;
+        const int wide = bg.tiles_x * bg.tiles_y;
+        const int per_seg = wide + bg.ntiles_y;
         const int seg = item.y / per_seg;
         const int rem = item.y - seg * per_seg;
-        const int by = rem / bg.tiles_x, bx = rem - by * bg.tiles_x;
         const int nz = bg.g.nz;
         const int kb = 1 + (int)(((long long)seg * nz) / bg.nseg);
         const int ke = (int)(((long long)(seg + 1) * nz) / bg.nseg);
         const CoefDev cf{bg.tcx, bg.tcy, bg.tz};
-        const CUtensorMap* m = maps + 3 * (size_t)item.x;
-        if (!march_tile<T, LX, TY, S, MODE_TEND, NC, RP, XP>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1],
-                                                           (T*)bg.o[2], bg.g, bg.ox, fold_coef(cf, sc), 0.f, bx, by,
-                                                           kb, ke, ring, err))
-            break;
+        const CUtensorMap* m = maps + B::MAPS * (size_t)item.x;
+        bool ok;
+        if (B::DUAL && rem >= wide) {
+            if constexpr (B::DUAL) {
+                MarchSmem<T, LX2, TY2, S, NC2, RP, XP> sn(smem_raw, B::RING);
+                ok = march_tile<T, LX2, TY2, S, MODE_TEND, NC2, RP, XP>(
+                    sn, m + 3, m + 4, m + 5, (T*)bg.o[0], (T*)bg.o[1], (T*)bg.o[2], bg.g, bg.ox, fold_coef(cf, sc),
+                    0.f, bg.nbx, rem - wide, kb, ke, ring, err);
+            } else {
+                ok = false;
+            }
+        } else {
+            const int by = rem / bg.tiles_x, bx = rem - by * bg.tiles_x;
+            ok = march_tile<T, LX, TY, S, MODE_TEND, NC, RP, XP>(sm, m, m + 1, m + 2, (T*)bg.o[0], (T*)bg.o[1],
+                                                                 (T*)bg.o[2], bg.g, bg.ox, fold_coef(cf, sc), 0.f,
+                                                                 bx, by, kb, ke, ring, err);
+        }
+        if (!ok) break;
     }
 }
 
@@ -91,27 +129,44 @@ __global__ void __launch_bounds__(TmaLayout<T, LX, TY, S, NC, RP, XP>::THREADS,
     X(16, 8, 4, 4, 1, 1) X(16, 4, 4, 8, 1, 1) X(16, 8, 4, 8, 1, 1) X(8, 8, 4, 8, 1, 1) X(8, 16, 4, 8, 1, 1)        \
     X(8, 16, 4, 4, 1, 0) X(32, 16, 4, 4, 1, 0)
 
-template <typename T, int LX, int TY, int S, int NC, int RP, int XP>
+// Wide shapes paired with a narrow last-column shape (the second triple:
+// lanes per row, rows, cells per thread; same stages, rows per thread and
+// pairing); the FP32 shapes (XP = 0) for FP32 storage, the x-pair ones for
+// 16-bit storage.
+#define PW_BATCH_DUALS(X) X(16, 16, 4, 4, 1, 0, 8, 32, 4) X(16, 8, 4, 4, 1, 0, 8, 16, 4) \
+    X(32, 8, 4, 4, 1, 0, 16, 16, 4) X(8, 16, 4, 8, 1, 1, 8, 16, 4) X(16, 8, 4, 8, 1, 1, 8, 16, 8)
+
+template <typename T, int LX, int TY, int S, int NC, int RP, int XP, int LX2 = 0, int TY2 = 0, int NC2 = 0>
 static cudaError_t batch_inst(bool query, int* bps, const BatchGridDev* grids, const CUtensorMap* maps,
                               const int2* items, int n_items, int* counter, const Scales& sc, int* err, int ctas,
                               cudaStream_t s) {
-  if constexpr (!nc_ok<T, NC, RP, XP>()) {
+  if constexpr (!nc_ok<T, NC, RP, XP>() || (NC2 > 0 && !nc_ok<T, NC2, RP, XP>()) ||
+                (NC2 > 0 && (XP == 0) != std::is_same<T, float>::value)) {
     return cudaErrorInvalidConfiguration;
   } else {
-    using L = TmaLayout<T, LX, TY, S, NC, RP, XP>;
-    auto kern = tma_batch_kernel<T, LX, TY, S, NC, RP, XP>;
-    cudaError_t e = set_smem_attr_once(kern, (int)L::SMEM);
+    using B = BatchShapes<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>;
+    auto kern = tma_batch_kernel<T, LX, TY, S, NC, RP, XP, LX2, TY2, NC2>;
+    cudaError_t e = set_smem_attr_once(kern, (int)B::SMEM);
     if (e != cudaSuccess) return e;
-    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, L::THREADS, L::SMEM);
-    kern<<<ctas, dim3(32, L::WARPS), L::SMEM, s>>>(grids, maps, items, n_items, counter, sc, err);
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, B::THREADS, B::SMEM);
+    kern<<<ctas, dim3(32, B::THREADS / 32), B::SMEM, s>>>(grids, maps, items, n_items, counter, sc, err);
     return cudaGetLastError();
   }
 }
 
 template <typename T>
-static cudaError_t batch_t(const TmaConfig& c, bool query, int* bps, const BatchGridDev* grids,
+static cudaError_t batch_t(const TmaConfig& c, bool dual, bool query, int* bps, const BatchGridDev* grids,
                            const CUtensorMap* maps, const int2* items, int n_items, int* counter, const Scales& sc,
                            int* err, int ctas, cudaStream_t s) {
+    if (dual) {
+#define PW_BDD(LX_, TY_, S_, NC_, RP_, XP_, LX2_, TY2_, NC2_)                                                 \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_)             \
+        return batch_inst<T, LX_, TY_, S_, NC_, RP_, XP_, LX2_, TY2_, NC2_>(query, bps, grids, maps, items, n_items, \
+                                                                            counter, sc, err, ctas, s);
+        PW_BATCH_DUALS(PW_BDD)
+#undef PW_BDD
+        return cudaErrorInvalidConfiguration;
+    }
 #define PW_BD(LX_, TY_, S_, NC_, RP_, XP_)                                                                     \
     if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_)             \
         return batch_inst<T, LX_, TY_, S_, NC_, RP_, XP_>(query, bps, grids, maps, items, n_items, counter, sc, err, \
@@ -121,14 +176,17 @@ static cudaError_t batch_t(const TmaConfig& c, bool query, int* bps, const Batch
     return cudaErrorInvalidConfiguration;
 }
 
-static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool query, int* bps,
+static cudaError_t batch_dispatch(pw_dtype_t dt, const TmaConfig& c, bool dual, bool query, int* bps,
                                   const BatchGridDev* grids, const CUtensorMap* maps, const int2* items, int n_items,
                                   int* counter, const Scales& sc, int* err, int ctas, cudaStream_t s) {
     switch (dt) {
-        case PW_F32: return batch_t<float>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+        case PW_F32:
+            return batch_t<float>(c, dual, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
         case PW_BF16:
-            return batch_t<__nv_bfloat16>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
-        case PW_F16: return batch_t<__half>(c, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
+            return batch_t<__nv_bfloat16>(c, dual, query, bps, grids, maps, items, n_items, counter, sc, err, ctas,
+                                          s);
+        case PW_F16:
+            return batch_t<__half>(c, dual, query, bps, grids, maps, items, n_items, counter, sc, err, ctas, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -140,6 +198,40 @@ static bool batch_config_supported(const TmaConfig& c, pw_dtype_t dt) {
     PW_BATCH_CONFIGS(PW_BS)
 #undef PW_BS
     return false;
+}
+
+// The narrow last-column shape paired with c for this storage type, if any.
+static bool narrow_partner(const TmaConfig& c, pw_dtype_t dt, TmaConfig* n) {
+#define PW_BN(LX_, TY_, S_, NC_, RP_, XP_, LX2_, TY2_, NC2_)                                                  \
+    if (c.lx == LX_ && c.ty == TY_ && c.stages == S_ && c.nc == NC_ && c.rp == RP_ && c.xp == XP_ &&           \
+        (XP_ == 0) == (dt == PW_F32)) {                                                                        \
+        *n = c;                                                                                                \
+        n->lx = LX2_;                                                                                          \
+        n->ty = TY2_;                                                                                          \
+        n->nc = NC2_;                                                                                          \
+        return true;                                                                                           \
+    }
+    PW_BATCH_DUALS(PW_BN)
+#undef PW_BN
+    return false;
+}
+
+// A grid's tiles: full-width columns, then its last column either as one
+// more wide column or, when it holds at most half a wide tile and a narrow
+// shape is in use, as a column of narrow tiles.
+struct TilePlan {
+    int tx, ty, nty, nbx;
+};
+static TilePlan tile_plan(const pw_grid_t& g, const TmaConfig& c, const TmaConfig* narrow) {
+    const int TX = c.nc * c.lx;
+    const int full = g.nx / TX, r = g.nx - full * TX;
+    TilePlan p{(g.nx + TX - 1) / TX, (g.ny + c.ty - 1) / c.ty, 0, 0};
+    if (narrow && r > 0 && r <= narrow->nc * narrow->lx) {
+        p.tx = full;
+        p.nty = (g.ny + narrow->ty - 1) / narrow->ty;
+        p.nbx = full * (TX / (narrow->nc * narrow->lx));
+    }
+    return p;
 }
 
 }  // namespace pw
@@ -165,6 +257,9 @@ struct pw_batch_s {
     std::vector<int2> items;
     long long cells = 0;
     TmaConfig cfg{32, 4, 4, 1};
+    bool narrow_on = true;  // narrow last columns where cfg has a narrow partner
+    bool dual = false;      // ... and it has one: ncfg
+    TmaConfig ncfg{0, 0, 0, 1};
     int ctas_per_sm = 0;    // 0 = occupancy
     int ctas = 0;
     std::vector<const void*> ptrs;   // 6n pointers the tables were built for
@@ -192,16 +287,15 @@ static void drop_graph(pw_batch_t b) {
 // the cost (a grid's ragged last column then ran with other grids' ones) and
 // 218 with y fastest.
 static pw_status_t build_items(pw_batch_t b) {
-    const int TX = b->cfg.nc * b->cfg.lx, TY = b->cfg.ty;
+    b->dual = b->narrow_on && narrow_partner(b->cfg, b->dtype, &b->ncfg);
     struct Item {
         int grid, tile;
         long long cost;
     };
     std::vector<Item> v;
     for (int q = 0; q < b->n; ++q) {
-        const pw_grid_t& g = b->grids[q];
-        const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
-        for (int t = 0; t < tx * ty; ++t) v.push_back({q, t, (long long)g.nz});
+        const TilePlan p = tile_plan(b->grids[q], b->cfg, b->dual ? &b->ncfg : nullptr);
+        for (int t = 0; t < p.tx * p.ty + p.nty; ++t) v.push_back({q, t, (long long)b->grids[q].nz});
     }
     std::stable_sort(v.begin(), v.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
     b->items.resize(v.size());
@@ -217,7 +311,7 @@ static pw_status_t build_items(pw_batch_t b) {
     if (e != cudaSuccess) return internal_cuda_fail(e, "batch work list upload");
     int bps = 0;
     Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
-    e = batch_dispatch(b->dtype, b->cfg, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
+    e = batch_dispatch(b->dtype, b->cfg, b->dual, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
                        nullptr);
     if (e != cudaSuccess || bps < 1) return internal_cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
                                                                "batch kernel occupancy");
@@ -303,12 +397,12 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t* grids, const pw_coeffs_t
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tz, tz.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, n * sizeof(BatchGridDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, 3 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, 6 * (size_t)n * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_grids, n * sizeof(BatchGridDev));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_maps, 3 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_maps, 6 * (size_t)n * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         pw_batch_destroy(b);
@@ -362,6 +456,21 @@ pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t cells, in
     return build_items(b);
 }
 
+pw_status_t pw_batch_set_narrow_columns(pw_batch_t b, int32_t enable) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (enable != 0 && enable != 1) return bfail(PW_ERR_ARG, "enable must be 0 or 1");
+    b->narrow_on = enable != 0;
+    return build_items(b);
+}
+
+pw_status_t pw_batch_narrow_shape(pw_batch_t b, int32_t* lanes_x, int32_t* cells, int32_t* ty) {
+    if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (lanes_x) *lanes_x = b->dual ? b->ncfg.lx : 0;
+    if (cells) *cells = b->dual ? b->ncfg.nc : 0;
+    if (ty) *ty = b->dual ? b->ncfg.ty : 0;
+    return PW_OK;
+}
+
 pw_status_t pw_batch_info(pw_batch_t b, int64_t* n_items, int64_t* cells, int32_t* ctas) {
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
     if (n_items) *n_items = (int64_t)b->items.size();
@@ -402,13 +511,16 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         // the pinned staging may still feed an earlier upload on this stream
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return internal_cuda_fail(e, "batch stream synchronize");
+        const int mps = b->dual ? 6 : 3;   // tensor maps per grid
         for (int q = 0; q < b->n; ++q) {
             const pw_grid_t& g = b->grids[q];
-            for (int a = 0; a < 3; ++a) {
-                pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a], b->cfg.lx, b->cfg.ty,
-                                                   &b->h_maps[3 * (size_t)q + a], b->cfg.nc, PW_BATCH_L2_PROMOTION);
+            for (int a = 0; a < mps; ++a) {
+                const TmaConfig& c = a < 3 ? b->cfg : b->ncfg;
+                pw_status_t st = encode_tensor_map(g, p[6 * (size_t)q + a % 3], c.lx, c.ty,
+                                                   &b->h_maps[mps * (size_t)q + a], c.nc, PW_BATCH_L2_PROMOTION);
                 if (st != PW_OK) return st;
             }
+            const TilePlan tp = tile_plan(g, b->cfg, b->dual ? &b->ncfg : nullptr);
             BatchGridDev& r = b->h_grids[q];
             r.g.nx = g.nx;
             r.g.ny = g.ny;
@@ -418,8 +530,10 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
             r.g.pk = g.pitch_k;
             r.g.origin = g.origin;
             r.ox = b->ox[q];
-            r.tiles_x = (g.nx + b->cfg.nc * b->cfg.lx - 1) / (b->cfg.nc * b->cfg.lx);
-            r.tiles_y = (g.ny + b->cfg.ty - 1) / b->cfg.ty;
+            r.tiles_x = tp.tx;
+            r.tiles_y = tp.ty;
+            r.ntiles_y = tp.nty;
+            r.nbx = tp.nbx;
             r.nseg = 1;
             r.tcx = b->tcx[q];
             r.tcy = b->tcy[q];
@@ -428,8 +542,8 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         }
         e = cudaMemcpyAsync(b->d_grids, b->h_grids, b->n * sizeof(BatchGridDev), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_maps, b->h_maps, 3 * (size_t)b->n * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
-                                s);
+            e = cudaMemcpyAsync(b->d_maps, b->h_maps, mps * (size_t)b->n * sizeof(CUtensorMap),
+                                cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return internal_cuda_fail(e, "batch table upload");
         b->ptrs = p;
         b->tables_ok = true;
@@ -442,7 +556,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
         if (e == cudaSuccess)
-            e = batch_dispatch(b->dtype, b->cfg, false, nullptr, b->d_grids, b->d_maps, b->d_items,
+            e = batch_dispatch(b->dtype, b->cfg, b->dual, false, nullptr, b->d_grids, b->d_maps, b->d_items,
                                (int)b->items.size(), b->d_counter, sc, b->d_err, b->ctas, b->cap);
         cudaGraph_t gr = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);

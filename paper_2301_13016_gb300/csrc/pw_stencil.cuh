@@ -470,7 +470,6 @@ __device__ __forceinline__ void march_level_core(MarchRegs<NC, V>& st, const Row
                 pxv[c] = O::add(Vv[c + 1], Vv[c + 2]);   // v(j,i) + v(j,i+1)
                 pys[c] = O::add(VS[c], VS[c + 1]);       // v(j-1,i) + v(j-1,i+1)
             }
-#pragma unroll
             pdx(F_U, st.pdu, false);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -713,13 +712,23 @@ struct TmaLayout {
     static constexpr bool PACKED = (RP == 2 || XP == 1);
     static constexpr bool CTAB = PACKED;
     static constexpr int CTAB_LEVELS = 128;
-    static constexpr size_t CTAB_OFF =
-        (((size_t)S * STAGE * sizeof(T) + S * sizeof(uint64_t) + 16 + 4 * S + 15) / 16) * 16;
+    static constexpr size_t CTAB_BYTES = CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0;
     // x-pair form with PW_MARCH_PD_SMEM: the lower flux products of every
     // thread (3 fields x NC/2 pairs) in shared memory between levels
     static constexpr bool PD_SMEM = XP == 1 && PW_MARCH_PD_SMEM;
-    static constexpr size_t PD_OFF = CTAB_OFF + (CTAB ? (size_t)CTAB_LEVELS * 3 * sizeof(float4) : 0);
-    static constexpr size_t SMEM = PD_OFF + (PD_SMEM ? (size_t)3 * (NC / 2) * THREADS * sizeof(float2) : 0);
+    static constexpr size_t PD_BYTES = PD_SMEM ? (size_t)3 * (NC / 2) * THREADS * sizeof(float2) : 0;
+    // The plane ring, then the mbarriers and flags, then the table and the
+    // flux products.  A kernel that marches tiles of two shapes through one
+    // ring gives both views the larger ring region (sb), so that the
+    // mbarriers sit at one address.
+    static constexpr size_t RING_BYTES = (size_t)S * STAGE * sizeof(T);
+    static constexpr size_t ctab_off(size_t sb) {
+        return ((sb + S * sizeof(uint64_t) + 16 + 4 * S + 15) / 16) * 16;
+    }
+    static constexpr size_t smem_bytes(size_t sb) { return ctab_off(sb) + CTAB_BYTES + PD_BYTES; }
+    static constexpr size_t CTAB_OFF = ctab_off(RING_BYTES);
+    static constexpr size_t PD_OFF = CTAB_OFF + CTAB_BYTES;
+    static constexpr size_t SMEM = smem_bytes(RING_BYTES);
     static_assert(LX == 32 || LX == 16 || LX == 8, "LX must be 8, 16 or 32");
     static_assert(NC == 4 || NC == 8, "4 or 8 cells per thread");
     static_assert(BW <= 256, "a TMA box is at most 256 elements wide");
@@ -758,13 +767,15 @@ struct MarchSmem {
     uint32_t* cnt;        // warps done with each slot's plane
     float4* ctab;         // vertical coefficient table (L::CTAB)
     float4* pd;           // lower flux products (L::PD_SMEM)
-    __device__ __forceinline__ MarchSmem(unsigned char* raw) {
-        pd = reinterpret_cast<float4*>(raw + L::PD_OFF);
+    // sb: bytes of the ring region (L::RING_BYTES, or more when the CTA also
+    // marches another shape through the same ring)
+    __device__ __forceinline__ explicit MarchSmem(unsigned char* raw, size_t sb = L::RING_BYTES) {
+        pd = reinterpret_cast<float4*>(raw + L::ctab_off(sb) + L::CTAB_BYTES);
         stages = reinterpret_cast<T*>(raw);
-        bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * L::STAGE * sizeof(T));
+        bars = reinterpret_cast<uint64_t*>(raw + sb);
         flag = reinterpret_cast<volatile int*>(bars + S);
         cnt = reinterpret_cast<uint32_t*>(bars + S) + 4;
-        ctab = reinterpret_cast<float4*>(raw + L::CTAB_OFF);
+        ctab = reinterpret_cast<float4*>(raw + L::ctab_off(sb));
     }
     // one thread, then a CTA barrier
     __device__ __forceinline__ void init(int tid) {

@@ -73,6 +73,9 @@ SIGNATURES = [
     ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
                                        ctypes.POINTER(_VP)]),
     ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
+    ("pw_batch_set_narrow_columns", ctypes.c_int, [_VP, _I32]),
+    ("pw_batch_narrow_shape", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]),
     ("pw_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(_I32)]),
     ("pw_batch_tendencies", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -437,6 +440,18 @@ class Batch:
         per thread along x (4, or 8 with x pairs when every nx allows)."""
         _check(lib().pw_batch_set_config(self.h, int(lanes_x), int(cells), int(ty), int(stages), int(ctas_per_sm),
                                          int(rows)), "pw_batch_set_config")
+
+    def set_narrow_columns(self, enable=True):
+        """March a grid's last column with tiles half as wide when it holds at
+        most half a tile (shapes with a narrow partner only; on by default)."""
+        _check(lib().pw_batch_set_narrow_columns(self.h, 1 if enable else 0), "pw_batch_set_narrow_columns")
+
+    def narrow_shape(self):
+        """The narrow shape in use, {"lanes_x", "cells", "ty"} (zeros: none)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().pw_batch_narrow_shape(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "pw_batch_narrow_shape")
+        return {"lanes_x": a.value, "cells": b.value, "ty": c.value}
 
     def info(self):
         ni, cells, ctas = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()

@@ -82,6 +82,62 @@ def test_batch_graph_replay_and_pointer_change():
             assert torch.allclose(x, y, rtol=0, atol=0, equal_nan=True)
 
 
+NARROW = [  # (lanes_x, ty, cells, rows, dtype) -> narrow (lanes_x, cells, ty)
+    ((16, 16, 4, 1, "f32"), (8, 4, 32)), ((16, 8, 4, 1, "f32"), (8, 4, 16)), ((32, 8, 4, 1, "f32"), (16, 4, 16)),
+    ((8, 16, 8, 3, "bf16"), (8, 4, 16)), ((16, 8, 8, 3, "bf16"), (8, 8, 16)), ((8, 16, 8, 3, "f16"), (8, 4, 16))]
+# last columns of every kind: none, narrow only (nx at most half a tile),
+# a narrow remainder, a wide remainder, exactly half a tile
+NARROW_SHAPES = [(16, 70, 5), (96, 33, 7), (100, 20, 4), (260, 9, 6), (4, 9, 3), (128, 17, 3), (32, 40, 8),
+                 (200, 18, 4)]
+
+
+@pytest.mark.parametrize("case", NARROW, ids=["x".join(map(str, c[0])) for c in NARROW])
+def test_batch_narrow_last_columns_same_bits(case):
+    """A grid's last column marched with tiles half as wide (the default for
+    the shapes that have a narrow partner) gives the bits of the uniform
+    tiling and of the single-grid kernel, and the work list holds exactly the
+    narrow tiles the tile plan implies."""
+    (lx, ty, cells, rows, dtype), (nlx, ncells, nty) = case
+    b, grids, coeffs, fields, dev, outs = _make_batch(NARROW_SHAPES, dtype=dtype)
+    b.set_config(lanes_x=lx, ty=ty, stages=4, rows=rows, cells=cells)
+    assert b.narrow_shape() == {"lanes_x": nlx, "cells": ncells, "ty": nty}
+    tw, tn = lx * cells, nlx * ncells
+    items = 0
+    for nx, ny, _ in NARROW_SHAPES:
+        full, r = divmod(nx, tw)
+        if 0 < r <= tn:
+            items += full * -(-ny // ty) + -(-ny // nty)
+        else:
+            items += -(-nx // tw) * -(-ny // ty)
+    assert b.info()["items"] == items
+    _run(b, dev, outs)
+    b.set_narrow_columns(False)
+    assert b.narrow_shape() == {"lanes_x": 0, "cells": 0, "ty": 0}
+    assert b.info()["items"] == sum(-(-nx // tw) * -(-ny // ty) for nx, ny, _ in NARROW_SHAPES)
+    outs2 = [[g.alloc(fill=NAN) for _ in range(3)] for g in grids]
+    _run(b, dev, outs2)
+    def same(g, x, y):   # interiors bit for bit (16-bit: whole arrays, NaN halos included)
+        if dtype == "f32":
+            return torch.equal(g.view(x)[1:-1, 1:-1, 1:-1], g.view(y)[1:-1, 1:-1, 1:-1])
+        return torch.equal(x.view(torch.int16), y.view(torch.int16))
+
+    for g, c, f, d, o, o2 in zip(grids, coeffs, fields, dev, outs, outs2):
+        h = pwlib.PW(g, c)
+        h.set_tma_config(ty, 4, 1, lanes_x=lx, cells=cells, rows=rows)
+        single = [g.alloc(fill=NAN) for _ in range(3)]
+        h.tendencies(*d, *single)
+        h.sync()
+        for x, y, z in zip(o, o2, single):
+            assert same(g, x, z) and same(g, x, y)
+        if dtype == "f32":
+            ref = oracle.tendencies(*[x.numpy() for x in f], c)
+            for x, r in zip(o, ref):
+                got = g.to_dense(x).numpy()
+                assert np.abs(interior(got) - interior(r)).max() <= 1e-5 * np.abs(interior(r)).max()
+    b.set_narrow_columns(True)
+    assert b.narrow_shape() == {"lanes_x": nlx, "cells": ncells, "ty": nty}
+
+
 PACKED = [(32, 8, 4, 4, 2), (16, 8, 4, 4, 2), (32, 8, 4, 4, 3), (16, 8, 4, 4, 3), (16, 8, 4, 8, 3),
           (16, 4, 4, 8, 3), (8, 8, 4, 8, 3), (8, 16, 4, 8, 3)]
 
