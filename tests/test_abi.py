@@ -99,6 +99,12 @@ def test_null_handle_is_rejected(L):
     assert L.pw_sync(None, None) == pwlib.PW_ERR_ARG
     assert L.pw_destroy(None) == pwlib.PW_OK
     assert L.pw_status_string(pwlib.PW_ERR_DEVICE_TIMEOUT) == b"PW_ERR_DEVICE_TIMEOUT"
+    # the batch's host-side entry points check their handle before any CUDA call
+    assert L.pw_batch_set_narrow_columns(None, 1) == pwlib.PW_ERR_ARG
+    assert L.pw_batch_narrow_shape(None, None, None, None) == pwlib.PW_ERR_ARG
+    assert L.pw_batch_set_config(None, 16, 4, 16, 4, 0, 1) == pwlib.PW_ERR_ARG
+    assert L.pw_batch_info(None, None, None, None) == pwlib.PW_ERR_ARG
+    assert L.pw_batch_destroy(None) == pwlib.PW_OK
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
