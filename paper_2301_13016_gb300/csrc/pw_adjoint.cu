@@ -230,6 +230,12 @@ __device__ __forceinline__ void adj_stv(float* p, const float (&v)[NA]) {
 #ifndef PW_ADJ_SPLIT_ARRIVE
 #define PW_ADJ_SPLIT_ARRIVE 0
 #endif
+// The first planes of a tile issued before (1) or after (0) the CTA fills its
+// table of vertical coefficients (4 x 6 shape: 98.5 against 96.4 Gcell/s at
+// 512^2 x 64, 127.8 against 127.0 at 2048^2, same box).
+#ifndef PW_ADJ_ISSUE_FIRST
+#define PW_ADJ_ISSUE_FIRST 1
+#endif
 
 // CTAs per SM a shape's register budget is sized for: what shared memory
 // allows, at most 2 for 4 cells a thread (their gather needs 165-182
@@ -290,6 +296,14 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
         abort_flag[0] = 0;
         fence_mbar_init();
     }
+    // the first planes go out before the coefficient table is filled, so that
+    // their DRAM latency overlaps the table's loads (the other threads wait
+    // on the planes' mbarriers only after the CTA barrier below)
+    if (PW_ADJ_ISSUE_FIRST && tid == 0) {
+        for (int f = 0; f < 6; ++f) prefetch_tensormap(&maps.m[f]);
+        for (; issued < S && issued < np; ++issued) issue(issued);
+        abort_flag[1] = issued;
+    }
     float4* const ctz = reinterpret_cast<float4*>(smem_raw + L::CTZ_OFF);   // entry k - (kb-1): level k
     for (int e = tid; e <= ke - kb + 2; e += 32 * TY) {
         const int k = kb - 1 + e;
@@ -297,7 +311,7 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
                              __ldg(cf.tz + 3 * nzp2 + k));
     }
     __syncthreads();
-    if (tid == 0) {
+    if (!PW_ADJ_ISSUE_FIRST && tid == 0) {
         for (int f = 0; f < 6; ++f) prefetch_tensormap(&maps.m[f]);
         for (; issued < S && issued < np; ++issued) issue(issued);
         abort_flag[1] = issued;
@@ -580,7 +594,10 @@ __global__ void __launch_bounds__(32 * TY, adj_min_blocks<NA, TY, S>())
 //            6 rows 93.9 / 113.8 / 121.3 (two CTAs of 6 warps per SM);
 //   2 cells: 4 rows 90.1 / 105.9 / 111.7, 5 rows 90.2 / 103.4 / 110.1,
 //            6 rows 84.5 / 98.7 / 104.0, 8 rows 82.4 / 95.1 / 102.5;
-// 3 slots (no plane in flight beyond k+1) lose a third.  Two cells a
+// 3 slots (no plane in flight beyond k+1) lose a third; 5 slots (two planes
+// in flight) gain nothing (4 x 4: 88.4 against 90.6, 2 x 8: 87.8 against
+// 86.3, 2 x 6: 91.0 against 90.8 at 512^2), so the march does not wait on
+// its planes' DRAM latency.  Two cells a
 // thread halve the registers (96 against 165-182) and double the warps per
 // SM, but that gains little: the gather is not bound by latency alone.
 #define PW_ADJ_CONFIGS(X) X(4, 5, 4) X(4, 4, 4) X(4, 6, 4) X(2, 4, 4) X(2, 5, 4) X(2, 6, 4) X(2, 8, 4) X(2, 8, 3)
