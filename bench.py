@@ -427,7 +427,11 @@ def run_ours(args, rank, world, local):
         f16 = lambda: h16.tendencies(*d16, *o16, stream=stream)
         for _ in range(3):
             f16()
+        h16.sync(stream)
+        assert h16.last_kernel == 2, "the BF16 leg must run the TMA k-march kernel"
+        TIMED_CLOCKS.clear()
         ms16 = _events_ms(f16, args.steps, stream)
+        clocks16 = timed_clocks_summary(TIMED_CLOCKS)
         h16.sync(stream)
         slab["outputs"]["bf16_max_rel_err"] = [g16.view(o)[1:-1, 1:rows + 1, 1:-1].double().cpu().numpy()
                                                for o in o16]
@@ -435,7 +439,7 @@ def run_ours(args, rank, world, local):
         bf16 = {"value": v16, "unit": "Gcell/s", "ms_per_step": ms16, "vs_fp32": v16 / (value / world),
                 "launch_shape": h16.tma_config(), "bytes_per_cell": 12,
                 "roofline_frac": 12 * cells / (ms16 / 1e3) / 1e9 / peak,
-                "stated_error_bound": 1e-2, "error": "cpu_baseline.parity.bf16_max_rel_err"}
+                "stated_error_bound": 1e-2, "error": "cpu_baseline.parity.bf16_max_rel_err", "clocks": clocks16}
         del h16, d16, o16
         torch.cuda.empty_cache()
 
@@ -505,7 +509,15 @@ def run_ours(args, rank, world, local):
 # Other forms of the path (one JSON line each, rank 0, N = 1): each is timed
 # beside the plain FP32 tendency kernel on the same GPU in the same process.
 
+TIMED_CLOCKS = []   # nvidia-smi clock records of the regions _events_ms timed (this process)
+
+
 def _events_ms(fn, n, stream):
+    """Mean ms per call of fn over n calls, CUDA events on `stream`, with the
+    SM clocks and throttle reasons sampled around the timed region."""
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -513,7 +525,20 @@ def _events_ms(fn, n, stream):
         fn()
     e1.record(stream)
     e1.synchronize()
+    c = sampler.stop()
+    if c:
+        TIMED_CLOCKS.append(c)
     return e0.elapsed_time(e1) / n
+
+
+def timed_clocks_summary(records):
+    """One clock record for several timed regions: the lowest median SM
+    clock, the highest maximum, every throttle reason seen."""
+    if not records:
+        return None
+    return {"sm_mhz": min(r["sm_mhz"] for r in records), "sm_max_mhz": max(r["sm_max_mhz"] for r in records),
+            "reasons": sorted(set().union(*[r["reasons"] for r in records])),
+            "samples": sum(r["samples"] for r in records), "regions": len(records)}
 
 
 def _fp32_reference_rate(nx, ny, nz, steps, stream):
@@ -540,6 +565,7 @@ def _form_line(args, form, metric, value, unit, config, extra):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic", "config": config}
     line.update(extra)
+    line.setdefault("clocks", timed_clocks_summary(TIMED_CLOCKS))
     line["version"] = source_version()
     print(json.dumps(line), flush=True)
 
@@ -638,14 +664,21 @@ def form_step(args, dtype, spp=1):
                extra)
 
 
-def form_batch(args, dtype="f32"):
+def form_batch(args, dtype="f32", rank=0, world=1):
+    """The batch of independent grids; under torchrun the grids are split
+    whole across the ranks (shard.assign_grids, no collective on the data
+    path), every rank marches its share in one batched launch, and the job is
+    timed by the slowest rank (strong scaling: the batch is fixed)."""
     import paper_2301_13016_gb300 as pwlib
-    from paper_2301_13016_gb300 import autotune, inputs
+    from paper_2301_13016_gb300 import autotune, inputs, shard
     stream = torch.cuda.current_stream()
-    ref = None if args.skip_fp32_ref else _fp32_reference_rate(2048, 2048, 64, 50, stream)
+    ref = None if (args.skip_fp32_ref or rank != 0) else _fp32_reference_rate(2048, 2048, 64, 50, stream)
     shapes = inputs.batch_shapes(n=args.batch_grids)
+    total_cells = sum(nx * ny * nz for nx, ny, nz in shapes)
+    mine = shard.assign_grids([nx * ny * nz for nx, ny, nz in shapes], world)[rank]
     grids, coeffs, dev, outs = [], [], [], []
-    for q, (nx, ny, nz) in enumerate(shapes):
+    for q in mine:
+        nx, ny, nz = shapes[q]
         g = pwlib.Grid(nx, ny, nz, dtype=dtype)
         c = inputs.make_coeffs(nz)
         d = inputs.random_fields(nx, ny, nz, device="cuda", seeds=(10 + 3 * q, 11 + 3 * q, 12 + 3 * q))
@@ -669,25 +702,38 @@ def form_batch(args, dtype="f32"):
     f = lambda: b.tendencies(*flds, stream=stream)
     for _ in range(args.warmup):
         f()
-    ms = _events_ms(f, args.steps, stream)
     b.sync(stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_own = _events_ms(f, args.steps, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    b.sync(stream)
+    ms = max_over_ranks(ms_own, world)
     info = b.info()
-    val = info["cells"] / (ms / 1e3) / 1e9
+    assert info["cells"] == sum(g.cells for g in grids)
+    if rank != 0:
+        return
+    val = total_cells / (ms / 1e3) / 1e9
     peak, kind = measured_peak()
     bpc = 24 if dtype == "f32" else 12
-    achieved = bpc * info["cells"] / (ms / 1e3) / 1e9
+    achieved = bpc * total_cells / (ms / 1e3) / 1e9
     n = args.batch_grids
     name = "batch" if dtype == "f32" else f"batch-{dtype}"
+    extra = {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
+             "autotune_s": tune_s, "autotune_ms": times,
+             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak * world, "unit": "GB/s",
+                          "frac": achieved / (peak * world), "peak_kind": kind, "bytes_per_cell": bpc},
+             "gpu_launches": args.steps}
+    if world > 1:
+        extra.update({"n_gpus": world, "scaling": "strong", "rank0_grids": len(mine), "rank0_cells": info["cells"]})
     _form_line(args, name, f"PW tendencies Gcell/s, {n} independent grids in one persistent graph-replayed launch",
                val, "Gcell/s", {"workload": f"{n} grids, nx, ny ~ U{{32..384 step 4}}, nz ~ U{{32..128}} (seed 2304), "
                                             f"{dtype.upper()} storage, FP32 math, random 10*N(0,1)",
-                                "cells": info["cells"], "items": info["items"], "ctas": info["ctas"], "tile": cfg,
-                                "narrow_last_columns": b.narrow_shape()},
-               {"dtype": dtype, "ms_per_step": ms, "vs_fp32_form": val / ref if ref else None, "fp32_form_gcells": ref,
-                "autotune_s": tune_s, "autotune_ms": times,
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_kind": kind, "bytes_per_cell": bpc},
-                "gpu_launches": args.steps})
+                                "cells": total_cells, "items": info["items"], "ctas": info["ctas"], "tile": cfg,
+                                "narrow_last_columns": b.narrow_shape(),
+                                "parallelism": f"{n} grids split whole over {world} GPU(s)"},
+               extra)
 
 
 def form_adjoint(args):
@@ -975,13 +1021,13 @@ def main():
             run_reference(args, rank, world)
         elif args.form == "tend":
             run_ours(args, rank, world, local)
+        elif args.form in ("batch", "batch-bf16"):
+            form_batch(args, "f32" if args.form == "batch" else "bf16", rank, world)
         elif rank == 0:
             {"tend-bf16": lambda: form_tend_lowp(args, "bf16"), "tend-f16": lambda: form_tend_lowp(args, "f16"),
              "step": lambda: form_step(args, "f32"), "step-bf16": lambda: form_step(args, "bf16"),
              "step2": lambda: form_step(args, "f32", 2), "step2-bf16": lambda: form_step(args, "bf16", 2),
              "step2-f16": lambda: form_step(args, "f16", 2),
-             "batch": lambda: form_batch(args),
-             "batch-bf16": lambda: form_batch(args, "bf16"),
              "adjoint": lambda: form_adjoint(args), "latency64": lambda: form_latency64(args),
              "hostlink": lambda: form_hostlink(args)}[args.form]()
     finally:

@@ -47,3 +47,13 @@ def test_committed_profile_is_parseable():
 def test_whole_job_rate_is_all_ranks_over_the_slowest():
     assert bench.whole_job_rate(100, 4, 2.0) == 200.0
     assert bench.whole_job_rate(100, 1, 0.5) == 200.0
+
+
+def test_clock_summary_keeps_the_worst_region():
+    """Several timed regions report one clock record: the lowest median SM
+    clock, the highest maximum and every throttle reason any region saw."""
+    recs = [{"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5},
+            {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}]
+    s = bench.timed_clocks_summary(recs)
+    assert s == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 9, "regions": 2}
+    assert bench.timed_clocks_summary([]) is None

@@ -68,3 +68,50 @@ def test_reference_arm_under_torchrun_prints_once():
     d = lines[0]
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _assign_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    import bench
+    from paper_2301_13016_gb300 import inputs, shard
+    bench.dist_init(_Args)
+    sizes = [nx * ny * nz for nx, ny, nz in inputs.batch_shapes()]
+    mine = shard.assign_grids(sizes, world)[rank]
+    got = [None] * world
+    dist.all_gather_object(got, mine)   # test only: the ranks never exchange this in the bench
+    q.put((rank, got))
+    dist.destroy_process_group()
+
+
+def test_batch_grids_split_whole_over_ranks():
+    """Every rank derives the same whole-grid assignment of the 512-grid batch
+    from the sizes alone: the ranks' lists are disjoint, cover every grid, and
+    the largest load exceeds the mean by less than one grid."""
+    from paper_2301_13016_gb300 import inputs, shard
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_assign_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    views = [g for _, g in got]
+    assert views[0] == views[1]                       # one assignment, derived independently
+    lists = views[0]
+    sizes = [nx * ny * nz for nx, ny, nz in inputs.batch_shapes()]
+    assert sorted(i for l in lists for i in l) == list(range(len(sizes)))
+    loads = [sum(sizes[i] for i in l) for l in lists]
+    assert max(loads) - sum(sizes) / 2 < max(sizes)
+    for world in (1, 3, 4, 8):
+        a = shard.assign_grids(sizes, world)
+        assert sorted(i for l in a for i in l) == list(range(len(sizes)))
+        ld = [sum(sizes[i] for i in l) for l in a]
+        assert max(ld) - sum(sizes) / world < max(sizes)
+    assert shard.assign_grids([5, 1, 1, 1], 2) == [[0], [1, 2, 3]]
