@@ -84,6 +84,11 @@ __global__ void __launch_bounds__((BatchShapes<T, LX, TY, S, NC, RP, XP, LX2, TY
     const int tid = threadIdx.y * 32 + threadIdx.x;
     sm.init(tid);
     uint32_t ring = 0;
+    // (Taking the next item while the current one marches measured slower:
+    // 512-grid batch FP32 7.77 -> 8.0-8.1 ms, BF16 5.51 -> 5.56-5.62 ms.  A
+    // tile then starts about a tile's time after it was taken, so raster
+    // neighbours no longer march together and share fewer halo rows in L2,
+    // and each CTA holds one more item at the end.)
     for (;;) {
         if (tid == 0) sm.flag[1] = atomicAdd(counter, 1);
         __syncthreads();
