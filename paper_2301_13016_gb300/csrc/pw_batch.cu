@@ -8,7 +8,9 @@
 // each grid's tiles stay together in raster order and neighbouring tiles
 // share their halo rows through L2), and a persistent k-march CTA per SM
 // slot takes the next item from an atomic counter until none is left, so
-// large and small grids share the GPU without a launch per grid.  The
+// large and small grids share the GPU without a launch per grid.  A grid's
+// last column of tiles, when it would hold at most half a tile, runs with
+// tiles half as wide through the same ring (narrow last columns).  The
 // per-grid records and TMA descriptors live in device tables that are
 // re-uploaded only when the field pointers change; the counter reset and the
 // kernel are captured once in a CUDA graph and replayed.
