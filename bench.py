@@ -41,7 +41,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pw_tend_tma_f32_2048x2048x64.m
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2301_13016_gb300", "csrc", f)
                   for f in ("pw_stencil.cuh", "pw_device.cuh", "pw_tend.cu")]
 FORMS = ["tend", "tend-bf16", "tend-f16", "step", "step-bf16", "step2", "step2-bf16", "step2-f16",
-         "batch", "batch-bf16", "adjoint", "latency64", "hostlink"]
+         "batch", "batch-bf16", "adjoint", "latency64", "hostlink", "step-slab"]
 
 
 def parse():
@@ -891,6 +891,57 @@ def _pitched_box_copies(rt, g, dst, src, i0, ni, j0, nj, chunks, kind, stream):
             raise RuntimeError("cudaMemcpy3DAsync failed")
 
 
+def form_step_slab(args, rank, world):
+    """Fused FP32 Euler steps of one 2048 x 2048 x 64 grid split in y slabs
+    over the ranks (slab.step_slabs: the step kernel per slab, then the
+    y-halo rows exchanged between neighbours; on one rank nothing is
+    exchanged).  Strong scaling: the grid is fixed, the job is timed by the
+    slowest rank."""
+    import paper_2301_13016_gb300 as pwlib
+    from paper_2301_13016_gb300 import inputs, slab
+    nx = ny = int(args.workload)
+    nz = 64
+    stream = torch.cuda.current_stream()
+    j0, nyr = slab.slab_rows(ny, world, rank)
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, nyr, nz)
+    h = pwlib.PW(g, c)
+    full = inputs.smooth_fields(nx, ny, nz, w_zero=True, device="cuda")
+    a = [g.from_dense(f[:, j0:j0 + nyr + 2, :]) for f in full]
+    del full
+    b = [g.alloc() for _ in range(3)]
+    ex = slab.HaloExchangeY(world, rank)
+    state = [a, b]
+
+    def f():
+        out = slab.step_slabs(h, g, state[0], state[1], 0.0, 2, ex, stream=stream)
+        if out[0] is not state[0][0]:
+            state.reverse()
+
+    for _ in range(max(1, args.warmup)):
+        f()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_own = _events_ms(f, max(1, args.steps // 2), stream) / 2
+    barrier(world)
+    ms = max_over_ranks(ms_own, world)
+    if rank != 0:
+        return
+    cells = nx * ny * nz
+    val = cells / (ms / 1e3) / 1e9
+    peak, kind = measured_peak()
+    achieved = 24 * cells / (ms / 1e3) / 1e9
+    _form_line(args, "step-slab", "PW fused forward-Euler step of one grid split in y slabs, Gcell-steps/s",
+               val, "Gcell-steps/s",
+               {"workload": f"{nx}x{ny}x{nz} smooth field (w = 0 initially), dt = 0 keeps the state fixed for timing",
+                "ranks": world, "rows_per_rank": [slab.slab_rows(ny, world, r)[1] for r in range(world)],
+                "parallelism": f"y slabs over {world} GPU(s), one y-halo row exchange per step"},
+               {"dtype": "f32", "ms_per_step": ms, "n_gpus": world, "scaling": "strong",
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak * world, "unit": "GB/s",
+                             "frac": achieved / (peak * world), "peak_kind": kind, "bytes_per_cell": 24},
+                "gpu_launches": 2 * max(1, args.steps // 2)})
+
+
 def form_hostlink(args):
     """The bound of the end-to-end number: the host link.  Measures the link's
     rate with plain copies of levels 1..nz of three fields between pinned
@@ -1028,6 +1079,8 @@ def main():
             run_ours(args, rank, world, local)
         elif args.form in ("batch", "batch-bf16"):
             form_batch(args, "f32" if args.form == "batch" else "bf16", rank, world)
+        elif args.form == "step-slab":
+            form_step_slab(args, rank, world)
         elif rank == 0:
             {"tend-bf16": lambda: form_tend_lowp(args, "bf16"), "tend-f16": lambda: form_tend_lowp(args, "f16"),
              "step": lambda: form_step(args, "f32"), "step-bf16": lambda: form_step(args, "bf16"),

@@ -223,3 +223,25 @@ def test_step_to_rejections():
     with pytest.raises(pwlib.PwError) as e:
         h.step_to(*q, *tmp, 1.0, scale=(1.0, 0.0, 1.0))
     assert e.value.status == pwlib.PW_ERR_ARG
+
+
+def test_slab_stepper_on_one_rank_equals_pw_step():
+    """The y-slab stepper (fused step kernel out of place, then the slab's
+    halo exchange) on a single rank holds the whole grid, exchanges nothing,
+    and gives pw_step's bits, halos included."""
+    from paper_2301_13016_gb300 import slab
+    nx, ny, nz, dt, n = 200, 37, 12, 1.0, 5
+    c = inputs.make_coeffs(nz)
+    g = pwlib.Grid(nx, ny, nz)
+    h = pwlib.PW(g, c)
+    f = inputs.smooth_fields(nx, ny, nz, w_zero=True)
+    a = [g.from_dense(x) for x in f]
+    b = [g.alloc(fill=NAN) for _ in range(3)]
+    assert slab.slab_rows(ny, 1, 0) == (0, ny)
+    out = slab.step_slabs(h, g, a, b, dt, n, slab.HaloExchangeY(1, 0))
+    ref = [g.from_dense(x) for x in f]
+    tmp = [g.alloc() for _ in range(3)]
+    h.step(*ref, *tmp, dt, n)
+    h.sync()
+    for x, y in zip(out, ref):
+        assert torch.equal(g.view(x)[1:-1], g.view(y)[1:-1])

@@ -115,3 +115,63 @@ def test_batch_grids_split_whole_over_ranks():
         ld = [sum(sizes[i] for i in l) for l in a]
         assert max(ld) - sum(sizes) / world < max(sizes)
     assert shard.assign_grids([5, 1, 1, 1], 2) == [[0], [1, 2, 3]]
+
+
+def _slab_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_2301_13016_gb300 import inputs, slab
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    nx, ny, nz, dt, nsteps = 12, 11, 6, 2.0, 5
+    c = inputs.make_coeffs(nz)
+    full = [f.double() for f in inputs.smooth_fields(nx, ny, nz)]        # periodic halos filled
+    j0, nyr = slab.slab_rows(ny, world, rank)
+    mine = [f[:, j0:j0 + nyr + 2, :].clone() for f in full]             # the slab with its halo rows
+    ex = slab.HaloExchangeY(world, rank)
+    for _ in range(nsteps):
+        # the local step: the oracle's source terms of the slab as it stands,
+        # the update, the x images; then the y-halo rows from the neighbours
+        s = oracle.tendencies(*[m.numpy() for m in mine], c)
+        for m, sm in zip(mine, s):
+            m[1:-1, 1:-1, 1:-1] += dt * torch.from_numpy(sm)[1:-1, 1:-1, 1:-1]
+            m[:, 1:-1, 0] = m[:, 1:-1, nx]
+            m[:, 1:-1, nx + 1] = m[:, 1:-1, 1]
+        ex.exchange(mine)
+    q.put((rank, j0, nyr, [m.numpy() for m in mine]))
+    dist.destroy_process_group()
+
+
+def test_slab_decomposed_steps_match_the_undivided_grid():
+    """Five Euler steps of one grid split in y over 2 and 3 gloo ranks (the
+    oracle's source terms per slab, the library's halo exchange between
+    them) give the undivided grid's oracle steps, halo rows included."""
+    import numpy as np
+    import oracle
+    from paper_2301_13016_gb300 import inputs, slab
+    nx, ny, nz, dt, nsteps = 12, 11, 6, 2.0, 5
+    c = inputs.make_coeffs(nz)
+    ref = oracle.step(*[f.double().numpy() for f in inputs.smooth_fields(nx, ny, nz)], c, dt, nsteps)
+    for world in (2, 3):
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        port = _free_port()
+        procs = [ctx.Process(target=_slab_main, args=(r, world, port, q)) for r in range(world)]
+        for p in procs:
+            p.start()
+        got = sorted((q.get(timeout=180) for _ in procs), key=lambda t: t[0])
+        for p in procs:
+            p.join(timeout=60)
+            assert p.exitcode == 0
+        assert [g[1] for g in got] == [slab.slab_rows(ny, world, r)[0] for r in range(world)]
+        assert sum(g[2] for g in got) == ny
+        for f in range(3):
+            for rank, j0, nyr, arrs in got:
+                a = arrs[f][1:-1, :, :]                          # levels 1..nz, halo rows and columns
+                r = ref[f][1:-1, j0:j0 + nyr + 2, :]
+                assert np.allclose(a, r, rtol=1e-12, atol=1e-12 * np.abs(ref[f]).max())
+    assert slab.slab_rows(10, 3, 0) == (0, 4) and slab.slab_rows(10, 3, 2) == (7, 3)
