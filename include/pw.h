@@ -470,6 +470,22 @@ pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream);
  */
 pw_status_t pw_selftest_wait_timeout(pw_handle_t h, int64_t limit_ns, pw_stream_t stream);
 
+/*
+ * Host-side failure injection for tests (no counterpart in the paper): the
+ * next `count` operations of one kind that the library performs fail as the
+ * CUDA call would have, before any call into CUDA:
+ *   kind 0: device or pinned host allocations (cudaMalloc, cudaMallocHost)
+ *           -> the entry point returns PW_ERR_OOM;
+ *   kind 1: TMA descriptor encodings (cuTensorMapEncodeTiled)
+ *           -> the entry point returns PW_ERR_CUDA.
+ * count = 0 clears the kind.  Process-wide, thread-safe; nothing reaches
+ * the GPU, so no kernel ever sees a failed allocation or descriptor.  Entry
+ * points that fail this way leave their handle as it was (no partial state
+ * is kept), and a later call succeeds.  PW_ERR_ARG for another kind or a
+ * negative count.
+ */
+pw_status_t pw_inject_failures(int32_t kind, int32_t count);
+
 /* Message for the last failure on this thread ("" if none). */
 const char *pw_last_error(void);
 

@@ -6,4 +6,5 @@ this package is its Python binding (pw.py) plus the seeded input generator
 """
 from .pw import (DTYPES, PW, Batch, Grid, PwError, lib, LIB_PATH, SIGNATURES,  # noqa: F401
                  PW_OK, PW_ERR_ARG, PW_ERR_ALIGN, PW_ERR_CUDA, PW_ERR_OOM, PW_ERR_DEVICE_TIMEOUT,
-                 PW_ERR_UNSUPPORTED, PW_ADJ_ACCUMULATE, PW_ADJ_PERIODIC, PW_ADJ_ADD_LAMBDA)
+                 PW_ERR_UNSUPPORTED, PW_ADJ_ACCUMULATE, PW_ADJ_PERIODIC, PW_ADJ_ADD_LAMBDA,
+                 INJECT_ALLOC, INJECT_TENSOR_MAP, inject_failures)

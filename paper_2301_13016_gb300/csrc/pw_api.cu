@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -204,6 +205,7 @@ pw_status_t pw::encode_tensor_map_box(const pw_grid_t& g, const void* ptr, int b
                                       int l2_promotion) {
     auto fn = encode_fn();
     if (!fn) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (inject_failure(INJECT_TENSOR_MAP)) return fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (injected)");
     int ox = 0;
     const char* why = "";
     if (!tma_layout_ok(g, &ox, &why)) return fail(PW_ERR_UNSUPPORTED, "layout not TMA-eligible: %s", why);
@@ -345,6 +347,15 @@ pw_status_t internal_fail(pw_status_t s, const char* fmt, ...) {
 
 pw_status_t internal_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
+static std::atomic<int> g_inject[INJECT_KINDS];
+
+bool inject_failure(int kind) {
+    int n = g_inject[kind].load(std::memory_order_relaxed);
+    while (n > 0)
+        if (g_inject[kind].compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+    return false;
+}
+
 cudaError_t set_smem_attr_once_impl(const void* kern, int bytes) {
     static std::mutex mu;
     static std::vector<std::pair<const void*, int>> done;   // (kernel, device)
@@ -427,9 +438,9 @@ pw_status_t pw_create(const pw_grid_t* grid, const pw_coeffs_t* coeffs, pw_handl
         tz[2 * n + k] = (float)coeffs->tzd1[k];
         tz[3 * n + k] = (float)coeffs->tzd2[k];
     }
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_tz, tz.size() * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&h->d_tz, tz.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(h->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
     // the upload and the clear run on the legacy default stream, which the
     // caller's non-blocking streams do not wait for: finish them here
@@ -711,7 +722,7 @@ static pw_status_t tendencies_host(pw_handle_t h, const void* u, const void* v, 
     const size_t bytes = (size_t)alloc_elems_of(g) * es;
     for (auto& p : h->d_stage)
         if (!p) {
-            cudaError_t e = cudaMalloc(&p, bytes);
+            cudaError_t e = dev_malloc(&p, bytes);
             if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging allocation");
             e = cudaMemsetAsync(p, 0, bytes, reinterpret_cast<cudaStream_t>(stream));   // before the copies
             if (e != cudaSuccess) return cuda_fail(e, "pw_tendencies_host staging clear");
@@ -1078,7 +1089,7 @@ static pw_status_t ensure_scratch(pw_handle_t h) {
     if (h->d_scratch) return PW_OK;
     h->nblocks = norm_blocks(h->num_sms);
     const size_t n = 4 * (size_t)(h->nblocks + 1) + (size_t)(h->grid.nz + 2);
-    cudaError_t e = cudaMalloc(&h->d_scratch, n * sizeof(double));
+    cudaError_t e = dev_malloc(&h->d_scratch, n * sizeof(double));
     if (e != cudaSuccess) {
         h->d_scratch = nullptr;
         return cuda_fail(e, "validation scratch allocation");
@@ -1148,6 +1159,13 @@ pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream) {
         return fail(PW_ERR_DEVICE_TIMEOUT, "a kernel gave up a bounded wait (code %d)", flag);
     }
     PW_CUDA(cudaGetLastError(), "pending CUDA error");
+    return PW_OK;
+}
+
+pw_status_t pw_inject_failures(int32_t kind, int32_t count) {
+    if (kind < 0 || kind >= INJECT_KINDS) return fail(PW_ERR_ARG, "kind must be 0 (allocations) or 1 (tensor maps)");
+    if (count < 0) return fail(PW_ERR_ARG, "count must be >= 0");
+    g_inject[kind].store(count, std::memory_order_relaxed);
     return PW_OK;
 }
 

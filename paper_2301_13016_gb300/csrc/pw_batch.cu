@@ -308,40 +308,54 @@ static void drop_graph(pw_batch_t b) {
 // 512-grid batch: 222 Gcell/s, against 212 when the tile width was part of
 // the cost (a grid's ragged last column then ran with other grids' ones) and
 // 218 with y fastest.
-static pw_status_t build_items(pw_batch_t b) {
-    b->dual = b->narrow_on && narrow_partner(b->cfg, b->dtype, &b->ncfg);
+// The work list of shape `cfg` is built and uploaded first and the batch
+// switched to it only when everything succeeded: on failure the batch keeps
+// its previous shape, work list and captured graph.
+static pw_status_t build_items(pw_batch_t b, const TmaConfig& cfg, int ctas_per_sm, bool narrow_on) {
+    TmaConfig ncfg{0, 0, 0, 1};
+    const bool dual = narrow_on && narrow_partner(cfg, b->dtype, &ncfg);
     struct Item {
         int grid, tile;
         long long cost;
     };
     std::vector<Item> v;
     for (int q = 0; q < b->n; ++q) {
-        const TilePlan p = tile_plan(b->grids[q], b->cfg, b->dual ? &b->ncfg : nullptr);
+        const TilePlan p = tile_plan(b->grids[q], cfg, dual ? &ncfg : nullptr);
         for (int t = 0; t < p.tx * p.ty + p.nty; ++t) v.push_back({q, t, (long long)b->grids[q].nz});
     }
     std::stable_sort(v.begin(), v.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
-    b->items.resize(v.size());
-    for (size_t i = 0; i < v.size(); ++i) b->items[i] = make_int2(v[i].grid, v[i].tile);
-    cudaFree(b->d_items);
-    b->d_items = nullptr;
-    cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(1, v.size()) * sizeof(int2));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_items, b->items.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    std::vector<int2> items(v.size());
+    for (size_t i = 0; i < v.size(); ++i) items[i] = make_int2(v[i].grid, v[i].tile);
+    int bps = 0;
+    Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
+    cudaError_t e = batch_dispatch(b->dtype, cfg, dual, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one,
+                                   nullptr, 0, nullptr);
+    if (e != cudaSuccess || bps < 1)
+        return internal_cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch kernel occupancy");
+    int2* d = nullptr;
+    e = dev_malloc(&d, std::max<size_t>(1, items.size()) * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(d, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
     // legacy-stream upload (and, at creation, the coefficient upload and the
     // status clear): complete before any launch on the caller's streams
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
-    if (e != cudaSuccess) return internal_cuda_fail(e, "batch work list upload");
-    int bps = 0;
-    Scales one{{1.f, 1.f, 1.f}, {1.f, 1.f, 1.f}};
-    e = batch_dispatch(b->dtype, b->cfg, b->dual, true, &bps, nullptr, nullptr, nullptr, 0, nullptr, one, nullptr, 0,
-                       nullptr);
-    if (e != cudaSuccess || bps < 1) return internal_cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
-                                                               "batch kernel occupancy");
-    const int per_sm = b->ctas_per_sm ? std::min(b->ctas_per_sm, bps) : bps;
-    b->ctas = PW_BATCH_GRID_LAUNCH ? std::max<int>(1, (int)v.size()) : b->num_sms * per_sm;
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return internal_cuda_fail(e, "batch work list upload");
+    }
+    // switch over (cudaFree waits for any launch still reading the old list)
+    drop_graph(b);
+    cudaFree(b->d_items);
+    b->d_items = d;
+    b->items.swap(items);
+    b->cfg = cfg;
+    b->ncfg = ncfg;
+    b->dual = dual;
+    b->narrow_on = narrow_on;
+    b->ctas_per_sm = ctas_per_sm;
+    const int per_sm = ctas_per_sm ? std::min(ctas_per_sm, bps) : bps;
+    b->ctas = PW_BATCH_GRID_LAUNCH ? std::max<int>(1, (int)b->items.size()) : b->num_sms * per_sm;
     b->items_ok = true;
     b->tables_ok = false;
-    drop_graph(b);
     return PW_OK;
 }
 
@@ -416,21 +430,21 @@ pw_status_t pw_batch_create(int32_t n, const pw_grid_t* grids, const pw_coeffs_t
     }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tz, tz.size() * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_tz, tz.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tz, tz.data(), tz.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, n * sizeof(BatchGridDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, 6 * (size_t)n * sizeof(CUtensorMap));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_grids, n * sizeof(BatchGridDev));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_maps, 6 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_grids, n * sizeof(BatchGridDev));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_maps, 6 * (size_t)n * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = host_malloc_pinned(&b->h_grids, n * sizeof(BatchGridDev));
+    if (e == cudaSuccess) e = host_malloc_pinned(&b->h_maps, 6 * (size_t)n * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         pw_batch_destroy(b);
         return internal_cuda_fail(e, "pw_batch_create");
     }
-    pw_status_t s = build_items(b);
+    pw_status_t s = build_items(b, b->cfg, 0, true);
     if (s != PW_OK) {
         pw_batch_destroy(b);
         return s;
@@ -473,16 +487,13 @@ pw_status_t pw_batch_set_config(pw_batch_t b, int32_t lanes_x, int32_t cells, in
                              "(dtype %d)",
                              c.lx, c.nc, c.ty, c.stages, rows_per_thread ? rows_per_thread : 1, (int)b->dtype);
     if (ctas_per_sm < 0) return bfail(PW_ERR_ARG, "ctas_per_sm must be >= 0");
-    b->cfg = c;
-    b->ctas_per_sm = ctas_per_sm;
-    return build_items(b);
+    return build_items(b, c, ctas_per_sm, b->narrow_on);
 }
 
 pw_status_t pw_batch_set_narrow_columns(pw_batch_t b, int32_t enable) {
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
     if (enable != 0 && enable != 1) return bfail(PW_ERR_ARG, "enable must be 0 or 1");
-    b->narrow_on = enable != 0;
-    return build_items(b);
+    return build_items(b, b->cfg, b->ctas_per_sm, enable != 0);
 }
 
 pw_status_t pw_batch_narrow_shape(pw_batch_t b, int32_t* lanes_x, int32_t* cells, int32_t* ty) {
@@ -506,6 +517,7 @@ pw_status_t pw_batch_tendencies(pw_batch_t b, const void* const* u, const void* 
                                 pw_stream_t stream) {
     PW_RANGE("pw_batch_tendencies");
     if (!b) return bfail(PW_ERR_ARG, "batch is NULL");
+    if (!b->items_ok || !b->d_items) return bfail(PW_ERR_ARG, "the batch has no work list");
     if (!u || !v || !w || !su || !sv || !sw) return bfail(PW_ERR_ARG, "a pointer table is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Scales sc;

@@ -178,6 +178,29 @@ cudaError_t launch_weighted_dot(pw_dtype_t dt, const GridDev& g, const void* a, 
 // Error reporting and handle access for translation units other than
 // pw_api.cu (set the thread-local message pw_last_error returns).
 pw_status_t internal_fail(pw_status_t s, const char* fmt, ...);
+
+// Host-side failure injection (pw_inject_failures): true when this operation
+// of `kind` is to fail (one pending failure consumed).
+enum { INJECT_ALLOC = 0, INJECT_TENSOR_MAP = 1, INJECT_KINDS = 2 };
+bool inject_failure(int kind);
+// cudaMalloc / cudaMallocHost, failing with cudaErrorMemoryAllocation (and a
+// null pointer) when an allocation failure is injected.
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+    if (inject_failure(INJECT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+template <class T>
+inline cudaError_t host_malloc_pinned(T** p, size_t bytes) {
+    if (inject_failure(INJECT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
 pw_status_t internal_cuda_fail(cudaError_t e, const char* what);
 bool internal_handle_grid(pw_handle_t h, pw_grid_t* g, int* num_sms);
 // The GPU a handle was created on.

@@ -70,6 +70,7 @@ SIGNATURES = [
                                                _dp, _VP]),
     ("pw_sync", ctypes.c_int, [_VP, _VP]),
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
+    ("pw_inject_failures", ctypes.c_int, [_I32, _I32]),
     ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
                                        ctypes.POINTER(_VP)]),
     ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),
@@ -111,6 +112,16 @@ def _check(status, what):
         msg = lib().pw_last_error().decode(errors="replace")
         name = lib().pw_status_string(status).decode()
         raise PwError(status, f"{what}: {name}: {msg}")
+
+
+INJECT_ALLOC, INJECT_TENSOR_MAP = 0, 1
+
+
+def inject_failures(kind, count):
+    """Host-side failure injection for tests: the library's next `count`
+    device or pinned allocations (INJECT_ALLOC) or TMA descriptor encodings
+    (INJECT_TENSOR_MAP) fail as the CUDA call would; count 0 clears."""
+    _check(lib().pw_inject_failures(int(kind), int(count)), "pw_inject_failures")
 
 
 def _stream_ptr(stream):

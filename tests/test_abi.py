@@ -107,6 +107,17 @@ def test_null_handle_is_rejected(L):
     assert L.pw_batch_destroy(None) == pwlib.PW_OK
 
 
+def test_failure_injection_arguments(L):
+    """pw_inject_failures takes kind 0 (allocations) or 1 (descriptor
+    encodings) and a count >= 0; count 0 clears (no GPU needed)."""
+    assert L.pw_inject_failures(2, 1) == pwlib.PW_ERR_ARG
+    assert L.pw_inject_failures(-1, 1) == pwlib.PW_ERR_ARG
+    assert L.pw_inject_failures(0, -1) == pwlib.PW_ERR_ARG
+    for kind in (0, 1):
+        assert L.pw_inject_failures(kind, 3) == pwlib.PW_OK
+        assert L.pw_inject_failures(kind, 0) == pwlib.PW_OK
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pwmod, "_LIB", None)
     monkeypatch.setattr(pwmod, "LIB_PATH", str(tmp_path / "missing.so"))
