@@ -486,6 +486,23 @@ pw_status_t pw_selftest_wait_timeout(pw_handle_t h, int64_t limit_ns, pw_stream_
  */
 pw_status_t pw_inject_failures(int32_t kind, int32_t count);
 
+/*
+ * Debug bounds build (the library compiled with -DPW_DEBUG_BOUNDS=1, e.g.
+ * PW_NVCC_EXTRA="-DPW_DEBUG_BOUNDS=1" python -m paper_2301_13016_gb300.build
+ * --force): every global store of the k-march and two-step kernels first
+ * checks its cells with the rule below; a store that fails is skipped and
+ * recorded, and the next pw_sync / pw_batch_sync returns PW_ERR_CUDA.  No
+ * device assert: a caught store never traps.  pw_debug_bounds_build returns
+ * 1 in such a build, else 0.
+ * pw_debug_layout_check applies the same rule on the host: 1 when the
+ * elements offset .. offset+n-1 (offsets from a field pointer, one row) lie
+ * on levels 1..nz and inside the interior (interior_only = 1) or the interior
+ * and its lateral halo (0), never in row padding or beyond; 0 otherwise; -1
+ * for an invalid grid or n < 1.
+ */
+int32_t pw_debug_bounds_build(void);
+int32_t pw_debug_layout_check(const pw_grid_t *g, int64_t offset, int32_t n, int32_t interior_only);
+
 /* Message for the last failure on this thread ("" if none). */
 const char *pw_last_error(void);
 

@@ -1156,11 +1156,20 @@ pw_status_t pw_sync(pw_handle_t h, pw_stream_t stream) {
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         PW_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s), "status word clear");
         PW_CUDA(cudaStreamSynchronize(s), "status word clear");
+        if (flag == DEV_OOB_STORE)
+            return fail(PW_ERR_CUDA, "a store outside the field's cells was caught and skipped (debug bounds build)");
         return fail(PW_ERR_DEVICE_TIMEOUT, "a kernel gave up a bounded wait (code %d)", flag);
     }
     PW_CUDA(cudaGetLastError(), "pending CUDA error");
     return PW_OK;
 }
+
+int32_t pw_debug_layout_check(const pw_grid_t* g, int64_t offset, int32_t n, int32_t interior_only) {
+    if (!g || validate_grid(g) != PW_OK || n < 1) return -1;
+    return layout_cells_ok(to_dev(*g), (long long)offset, n, interior_only != 0) ? 1 : 0;
+}
+
+int32_t pw_debug_bounds_build(void) { return PW_DEBUG_BOUNDS ? 1 : 0; }
 
 pw_status_t pw_inject_failures(int32_t kind, int32_t count) {
     if (kind < 0 || kind >= INJECT_KINDS) return fail(PW_ERR_ARG, "kind must be 0 (allocations) or 1 (tensor maps)");

@@ -619,6 +619,9 @@ pw_status_t pw_batch_sync(pw_batch_t b, pw_stream_t stream) {
     if (flag != DEV_OK) {
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         if (cudaMemsetAsync(b->d_err, 0, sizeof(int), s) == cudaSuccess) cudaStreamSynchronize(s);
+        if (flag == DEV_OOB_STORE)
+            return internal_fail(PW_ERR_CUDA,
+                                 "a store outside the field's cells was caught and skipped (debug bounds build)");
         return internal_fail(PW_ERR_DEVICE_TIMEOUT, "a batched kernel gave up a bounded wait (code %d)", flag);
     }
     return PW_OK;

@@ -135,6 +135,7 @@ enum : int {
     DEV_OK = 0,
     DEV_TIMEOUT_TMA_WAIT = 1,   // an mbarrier wait for a TMA copy ran out of time
     DEV_TIMEOUT_QUEUE = 2,      // a work-queue wait ran out of time
+    DEV_OOB_STORE = 3,          // debug bounds build: a store outside the field's cells was skipped
 };
 
 // Wait limit for any spin in these kernels (nanoseconds of %globaltimer).

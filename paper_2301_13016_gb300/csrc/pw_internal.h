@@ -43,6 +43,25 @@ struct GridDev {
     long long pj, pk, origin;
 };
 
+// Cells o .. o+n-1 of a field (element offsets from the field pointer, one
+// row) lie on levels 1..nz and inside the interior (interior_only) or the
+// interior and its lateral halo, never in row padding or beyond: the check of
+// the debug bounds build, on the host and the device alike.
+#ifndef PW_DEBUG_BOUNDS
+#define PW_DEBUG_BOUNDS 0
+#endif
+__host__ __device__ inline bool layout_cells_ok(const GridDev& g, long long o, int n, bool interior_only) {
+    const int h = g.halo;
+    const long long rel = o - g.origin - (long long)(1 - h) * g.pj - (1 - h);   // from (k, 1-h, 1-h)
+    if (rel < 0 || n < 1) return false;
+    const long long k = rel / g.pk, r = rel - k * g.pk;
+    const long long jj = r / g.pj, ii = r - jj * g.pj;
+    const long long j = jj + 1 - h, i0 = ii + 1 - h, i1 = i0 + n - 1;
+    if (k < 1 || k > g.nz) return false;
+    if (interior_only) return j >= 1 && j <= g.ny && i0 >= 1 && i1 <= g.nx;
+    return j <= g.ny + h && i1 <= g.nx + h;
+}
+
 // Per-field storage scales: physical = stored * in[f]; stored = physical * out[f].
 struct Scales {
     float in[3];

@@ -14,6 +14,24 @@ namespace pw {
 
 enum { MODE_TEND = 0, MODE_STEP = 1 };
 
+// Debug bounds build (PW_DEBUG_BOUNDS=1): every global store of the k-march
+// and two-step kernels first checks that its cells lie where the kernel may
+// write (layout_cells_ok: levels 1..nz, the interior for source terms and
+// state, the lateral halo for periodic images, never row padding); a store
+// that does not is skipped and recorded in the status word (DEV_OOB_STORE,
+// reported by pw_sync).  Nothing is asserted, so a caught store never traps.
+// (PW_DEBUG_BOUNDS defaults to 0 in pw_internal.h.)
+// false (and the store is to be skipped) when the debug build catches it
+__device__ __forceinline__ bool dbg_store(const GridDev& g, long long o, int n, bool interior_only, int* err) {
+    if constexpr (PW_DEBUG_BOUNDS) {
+        if (!layout_cells_ok(g, o, n, interior_only)) {
+            if (err) atomicCAS(err, DEV_OK, DEV_OOB_STORE);
+            return false;
+        }
+    }
+    return true;
+}
+
 // Writes the three outputs of one cell or one row vector of N cells, plus the
 // periodic images (MODE_STEP) when the cells lie near the lateral boundary.  o = offset of (k, j, i0); cells i0..i0+n-1.
 template <typename T, int MODE>
@@ -29,9 +47,9 @@ struct Epilogue<T, MODE_TEND> {
     }
     // one field's row vector of N cells
     template <int N>
-    static __device__ __forceinline__ void store_field(T* of, long long o, const float (&a)[N], const GridDev&, int,
-                                                       int) {
-        storev<N>(of + o, a);
+    static __device__ __forceinline__ void store_field(T* of, long long o, const float (&a)[N], const GridDev& g, int,
+                                                       int, int* err = nullptr) {
+        if (dbg_store(g, o, N, true, err)) storev<N>(of + o, a);
     }
 };
 
@@ -70,7 +88,7 @@ struct StepImages {
     // one field's vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
     template <typename T, int N>
     static __device__ __forceinline__ void vec1(T* of, long long o, const float (&a)[N], const GridDev& g, int j,
-                                                int i0) {
+                                                int i0, int* err = nullptr) {
         const int H = g.halo;
         const bool west = (i0 <= H), east = (i0 + N - 1 > g.nx - H);
         const long long dyp = (j <= H) ? (long long)g.ny * g.pj : 0;
@@ -81,12 +99,14 @@ struct StepImages {
         for (int s = 0; s < 3; ++s) {
             if (s > 0 && shifts[s] == 0) continue;
             const long long p = o + shifts[s];
-            if (s > 0) storev<N>(of + p, a);   // the row image
+            if (s > 0 && dbg_store(g, p, N, false, err)) storev<N>(of + p, a);   // the row image
 #pragma unroll
             for (int q = 0; q < N; ++q) {
                 const int i = i0 + q;
-                if (west && i <= H) of[p + q + g.nx] = Store<T>::from_f(a[q]);       // i -> i + nx
-                if (east && i > g.nx - H) of[p + q - g.nx] = Store<T>::from_f(a[q]); // i -> i - nx
+                if (west && i <= H && dbg_store(g, p + q + g.nx, 1, false, err))
+                    of[p + q + g.nx] = Store<T>::from_f(a[q]);   // i -> i + nx
+                if (east && i > g.nx - H && dbg_store(g, p + q - g.nx, 1, false, err))
+                    of[p + q - g.nx] = Store<T>::from_f(a[q]);   // i -> i - nx
             }
         }
     }
@@ -110,8 +130,8 @@ struct Epilogue<T, MODE_STEP> {
     // one field's vector of N cells (j, i0..i0+N-1), i0 = 1 mod N, nx = 0 mod N
     template <int N>
     static __device__ __forceinline__ void store_field(T* of, long long o, const float (&a)[N], const GridDev& g,
-                                                       int j, int i0) {
-        storev<N>(of + o, a);
+                                                       int j, int i0, int* err = nullptr) {
+        if (dbg_store(g, o, N, true, err)) storev<N>(of + o, a);
         if (g.halo != 1) return;   // deeper halos are refreshed by the halo kernel
         const bool west = (i0 == 1), east = (i0 + N - 1 == g.nx);
         // most row vectors touch no boundary: one test, the same at every level
@@ -123,9 +143,11 @@ struct Epilogue<T, MODE_STEP> {
         for (int s = 0; s < 3; ++s) {
             if (s > 0 && shifts[s] == 0) continue;
             const long long p = o + shifts[s];
-            if (s > 0) storev<N>(of + p, a);                                   // the row image
-            if (west) of[p + g.nx] = Store<T>::from_f(a[0]);                  // cell i = 1 -> i = nx+1
-            if (east) of[p + (N - 1) - g.nx] = Store<T>::from_f(a[N - 1]);    // cell i = nx -> i = 0
+            if (s > 0 && dbg_store(g, p, N, false, err)) storev<N>(of + p, a);   // the row image
+            if (west && dbg_store(g, p + g.nx, 1, false, err))
+                of[p + g.nx] = Store<T>::from_f(a[0]);                  // cell i = 1 -> i = nx+1
+            if (east && dbg_store(g, p + (N - 1) - g.nx, 1, false, err))
+                of[p + (N - 1) - g.nx] = Store<T>::from_f(a[N - 1]);    // cell i = nx -> i = 0
         }
     }
 };
@@ -1040,11 +1062,11 @@ __device__ __forceinline__ bool march_tile(const MarchSmem<T, LX, TY, S, NC, RP,
                         // padding columns and are not stored)
                         if (i0 + NC - 1 > g.nx) {
                             const float h4[4] = {a[0], a[1], a[2], a[3]};
-                            storev<4>(of + o, h4);
+                            if (dbg_store(g, o, 4, true, err)) storev<4>(of + o, h4);
                             return;
                         }
                     }
-                    Epilogue<T, MODE>::template store_field<NC>(of, o, a, g, j + half, i0);
+                    Epilogue<T, MODE>::template store_field<NC>(of, o, a, g, j + half, i0, err);
                 };
                 if (valid) field_row(0);
                 if (RP == 2 && valid2) field_row(1);

@@ -215,12 +215,14 @@ __global__ void __launch_bounds__(Tb2Layout<T, TY, S>::THREADS, (tb2_min_blocks<
                     d[c] = fmaf(dt, rw[c], w1[c]);
                 }
                 const long long o = row_off + (long long)m * g.pk;
-                storev<NC>(o0 + o, a);
-                storev<NC>(o1 + o, b);
-                storev<NC>(o2 + o, d);
-                StepImages::vec1<T, NC>(o0, o, a, g, j, i0);
-                StepImages::vec1<T, NC>(o1, o, b, g, j, i0);
-                StepImages::vec1<T, NC>(o2, o, d, g, j, i0);
+                if (dbg_store(g, o, NC, true, err)) {
+                    storev<NC>(o0 + o, a);
+                    storev<NC>(o1 + o, b);
+                    storev<NC>(o2 + o, d);
+                }
+                StepImages::vec1<T, NC>(o0, o, a, g, j, i0, err);
+                StepImages::vec1<T, NC>(o1, o, b, g, j, i0, err);
+                StepImages::vec1<T, NC>(o2, o, d, g, j, i0, err);
             };
             march_level<NC, 32>(st2, rowld2, edgeld2, out2, lane, m == kb1, m + 1 <= ke1, (m >= kb) && (m >= 2), kc,
                                 m, nzp2);

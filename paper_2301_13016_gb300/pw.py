@@ -71,6 +71,8 @@ SIGNATURES = [
     ("pw_sync", ctypes.c_int, [_VP, _VP]),
     ("pw_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
     ("pw_inject_failures", ctypes.c_int, [_I32, _I32]),
+    ("pw_debug_bounds_build", ctypes.c_int32, []),
+    ("pw_debug_layout_check", ctypes.c_int32, [ctypes.POINTER(pw_grid_t), ctypes.c_int64, _I32, _I32]),
     ("pw_batch_create", ctypes.c_int, [_I32, ctypes.POINTER(pw_grid_t), ctypes.POINTER(pw_coeffs_t),
                                        ctypes.POINTER(_VP)]),
     ("pw_batch_set_config", ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32, _I32]),

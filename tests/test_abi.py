@@ -123,3 +123,38 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pwmod, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         pwmod.lib()
+
+
+def test_debug_layout_check_matches_the_layout(L):
+    """The rule the debug bounds build applies to every store, on the host:
+    cells of levels 1..nz, interior (or interior plus lateral halo), never
+    row padding or the z-halo planes."""
+    g = pwmod.pw_grid_t()
+    n_elems = ctypes.c_int64()
+    assert L.pw_grid_default(100, 7, 5, 1, 0, ctypes.byref(g), ctypes.byref(n_elems)) == pwlib.PW_OK
+    off = lambda k, j, i: g.origin + k * g.pitch_k + j * g.pitch_j + i
+    chk = lambda o, n, inner: L.pw_debug_layout_check(ctypes.byref(g), o, n, inner)
+    assert g.pitch_j > g.nx + 2                          # the default layout pads its rows
+    for k in (1, 3, 5):
+        assert chk(off(k, 1, 1), 4, 1) == 1               # an interior vector
+        assert chk(off(k, 7, 97), 4, 1) == 1              # the row's last one
+        assert chk(off(k, 7, 98), 4, 1) == 0              # one cell past the interior
+        assert chk(off(k, 7, 98), 4, 0) == 1              # ... which the halo allows
+        assert chk(off(k, 7, 98), 5, 0) == 0              # ... but not into the padding
+        assert chk(off(k, 0, 0), 1, 0) == 1 and chk(off(k, 0, 0), 1, 1) == 0   # a halo corner
+        assert chk(off(k, 8, 101), 1, 0) == 1              # the top halo row's last cell
+        assert chk(off(k, 3, 102), 1, 0) == 0            # row padding
+    assert chk(off(0, 1, 1), 1, 0) == 0 and chk(off(6, 1, 1), 1, 0) == 0   # z-halo planes
+    assert chk(off(1, 1, 1) - 10 ** 6, 1, 0) == 0 and chk(off(1, 1, 1), 0, 0) == -1
+    g2 = pwmod.pw_grid_t()
+    assert L.pw_grid_default(64, 9, 4, 2, 1, ctypes.byref(g2), ctypes.byref(n_elems)) == pwlib.PW_OK
+    off2 = lambda k, j, i: g2.origin + k * g2.pitch_k + j * g2.pitch_j + i
+    assert L.pw_debug_layout_check(ctypes.byref(g2), off2(2, -1, -1), 1, 0) == 1   # halo 2 corner
+    assert L.pw_debug_layout_check(ctypes.byref(g2), off2(2, 11, 66), 1, 0) == 1
+    assert L.pw_debug_layout_check(ctypes.byref(g2), off2(2, 5, 67), 1, 0) == 0   # row padding
+    # a layout with a padding row between levels: that row is never writable
+    g3 = pwmod.pw_grid_t(100, 7, 5, 1, 160, 160 * 10, 31, 0)
+    off3 = lambda k, j, i: g3.origin + k * g3.pitch_k + j * g3.pitch_j + i
+    assert L.pw_debug_layout_check(ctypes.byref(g3), off3(3, 8, 1), 1, 0) == 1
+    assert L.pw_debug_layout_check(ctypes.byref(g3), off3(3, 9, 1), 1, 0) == 0
+    assert L.pw_debug_bounds_build() in (0, 1)
