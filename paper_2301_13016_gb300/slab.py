@@ -72,9 +72,12 @@ class HaloExchangeY:
 def step_slabs(h, grid, q, nq, dt, nsteps, exchange, scale=None, stream=None):
     """nsteps forward-Euler steps of the rank's slab: the fused step kernel
     out of place (q -> nq), then the y-halo exchange of the new state.  q
-    (three fields of `grid`) must hold the slab with its halos filled as the
-    undivided grid's would be (`exchange` after a periodic fill does that).
-    Returns the three fields that hold the final state (q or nq)."""
+    (three fields of `grid`, a one-cell lateral halo: the scheme's reach)
+    must hold the slab with its halos filled as the undivided grid's would
+    be (`exchange` after a periodic fill does that).  Returns the three
+    fields that hold the final state (q or nq)."""
+    if grid.halo != 1:
+        raise ValueError("the slab exchange moves one halo row: the grid needs halo = 1")
     a, b = list(q), list(nq)
     for _ in range(nsteps):
         h.step_to(*a, *b, dt, scale=scale, stream=stream)
